@@ -1,0 +1,32 @@
+"""FP64 CPU oracle for the non-Fourier SENSE operator, its CG solve and its B0 gradient.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import it; the product path never does. It
+shares no code with the CUDA library. The arithmetic lives in ``sense_oracle.c`` (plain
+complex128 loops); this module only loads it and marshals numpy arrays.
+
+Functions and the passages they follow:
+  encode       Eq. 4   s = P (S o (m 1^T)), P = e^{o iKR}, S <- S o j (Fig. 2 Alg. 1 step 1)
+  adjoint      Eq. 5   m = (S* o (P^H Sigma)) 1
+  normal       E^H E m (Fig. 2 Alg. 1 step 8)
+  cg           Fig. 2 Alg. 1 steps 3-18
+  grad_omega   chain rule of Eq. 4 w.r.t. row 0 of R (the B0 map)
+  lcurve_corner  maximum-curvature point of the L-curve (log residual norm vs log
+                 solution norm over CG iterations), the stopping rule the paper evaluates
+
+Each is pinned in tests/test_oracle_pins.py against results the paper and the mathematics
+fix: a closed-form DFT, a point source, adjointness, a dense normal-equation solve, Krylov
+minimisation of early iterates, finite differences, and an analytic curvature.
+"""
+from .oracle import (  # noqa: F401
+    build,
+    load,
+    encode,
+    adjoint,
+    normal,
+    cg,
+    grad_omega,
+    lcurve_corner,
+    num_threads,
+    set_num_threads,
+)

@@ -1,0 +1,189 @@
+"""ctypes loader and numpy marshalling for the FP64 oracle (``sense_oracle.c``).
+
+Test infrastructure only; see the package docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sense_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_ptr = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile sense_oracle.c with gcc into liboracle.so (OpenMP, -O2, no fast-math)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.or_num_threads.restype = _int
+        lib.or_set_num_threads.argtypes = [_int]
+        lib.or_encode.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
+                                  _i64, _ptr]
+        lib.or_adjoint.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
+                                   _i64, _ptr]
+        lib.or_normal.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
+                                  _ptr]
+        lib.or_cg.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _int, _dbl,
+                              _int, _ptr, _ptr, _ptr]
+        lib.or_cg.restype = _int
+        lib.or_grad_omega.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
+                                      _ptr]
+        _lib = lib
+        return lib
+
+
+def num_threads() -> int:
+    return int(load().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    load().or_set_num_threads(int(n))
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _geom(Kmat, Rmat, S, j):
+    Kmat = _c(Kmat, np.float64)
+    Rmat = _c(Rmat, np.float64)
+    S = _c(S, np.complex128)
+    K, P1 = Kmat.shape
+    P1b, L = Rmat.shape
+    if P1b != P1:
+        raise ValueError("K has %d columns but R has %d rows" % (P1, P1b))
+    if S.shape[0] != L:
+        raise ValueError("S must be [L][C]")
+    jj = None if j is None else _c(j, np.float64)
+    if jj is not None and jj.shape != (L,):
+        raise ValueError("j must be [L]")
+    return Kmat, Rmat, S, jj, L, K, S.shape[1], P1
+
+
+def encode(Kmat, Rmat, S, m, j=None, rows=None):
+    """s = E m (Eq. 4); rows selects sample indices (default all)."""
+    Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
+    m = _c(m, np.complex128)
+    if rows is None:
+        r, n = None, K
+    else:
+        r = _c(rows, np.int64)
+        n = r.shape[0]
+    out = np.empty((n, C), np.complex128)
+    load().or_encode(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(m), _p(r), n, _p(out))
+    return out
+
+
+def adjoint(Kmat, Rmat, S, s, j=None, vox=None):
+    """m = E^H s (Eq. 5); vox selects voxel indices (default all)."""
+    Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
+    s = _c(s, np.complex128).reshape(K, C)
+    if vox is None:
+        v, n = None, L
+    else:
+        v = _c(vox, np.int64)
+        n = v.shape[0]
+    out = np.empty(n, np.complex128)
+    load().or_adjoint(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(s), _p(v), n, _p(out))
+    return out
+
+
+def normal(Kmat, Rmat, S, m, j=None):
+    """E^H E m."""
+    Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
+    m = _c(m, np.complex128)
+    out = np.empty(L, np.complex128)
+    work = np.empty(K * C, np.complex128)
+    load().or_normal(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(m), _p(out), _p(work))
+    return out
+
+
+def cg(Kmat, Rmat, S, sigma, n_it, j=None, rel_tol=0.0, apply_j=True, history=False,
+       iterates=False):
+    """Fig. 2 Alg. 1 steps 3-18. Returns dict(x, iters, history?, iterates?)."""
+    Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
+    sigma = _c(sigma, np.complex128).reshape(K, C)
+    rho = np.empty(L, np.complex128)
+    hist = np.full((n_it + 1, 3), np.nan) if history else None
+    its = np.zeros((n_it + 1, L), np.complex128) if iterates else None
+    n = load().or_cg(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(sigma), int(n_it),
+                     float(rel_tol), 1 if apply_j else 0, _p(rho), _p(hist), _p(its))
+    out = {"x": rho, "iters": int(n)}
+    if history:
+        out["history"] = hist[: n + 1]
+    if iterates:
+        out["iterates"] = its[: n + 1]
+    return out
+
+
+def grad_omega(Kmat, Rmat, S, m, g, j=None):
+    """d Loss / d R[0,:] given g = dLoss/dRe(Em) + i dLoss/dIm(Em)."""
+    Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
+    m = _c(m, np.complex128)
+    g = _c(g, np.complex128).reshape(K, C)
+    out = np.empty(L, np.float64)
+    load().or_grad_omega(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(m), _p(g),
+                         _p(out))
+    return out
+
+
+def lcurve_corner(res_norm, sol_norm):
+    """Index n (into the given arrays) of maximum L-curve curvature.
+
+    The L-curve is the parametric curve (a, b) = (log ||E x_n - s||, log ||x_n||) over the
+    CG iterations n; the proposed stop is its point of maximum curvature. CG first moves
+    along the flat leg (the residual falls) and then up the steep leg (the solution norm
+    grows), so the corner is a clockwise turn; the curvature is signed positive for
+    clockwise turns: kappa = (a'' b' - a' b'') / (a'^2 + b'^2)^1.5, derivatives by central
+    differences in n. Only interior points are candidates and the first maximum wins.
+    Returns -1 when fewer than three points are given.
+    """
+    a = np.log(np.asarray(res_norm, np.float64))
+    b = np.log(np.asarray(sol_norm, np.float64))
+    n = a.shape[0]
+    if n < 3:
+        return -1
+    best, best_k = -1, -np.inf
+    for i in range(1, n - 1):
+        da = 0.5 * (a[i + 1] - a[i - 1])
+        db = 0.5 * (b[i + 1] - b[i - 1])
+        dda = a[i + 1] - 2.0 * a[i] + a[i - 1]
+        ddb = b[i + 1] - 2.0 * b[i] + b[i - 1]
+        den = (da * da + db * db) ** 1.5
+        if den == 0.0:
+            continue
+        k = (dda * db - da * ddb) / den
+        if k > best_k:
+            best, best_k = i, k
+    return best

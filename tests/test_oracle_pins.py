@@ -1,0 +1,227 @@
+"""Pins of the FP64 oracle against results the paper and the mathematics fix.
+
+None of these re-types the oracle's loops. Each targets a class of plausible mistake:
+  closed-form DFT (numpy FFT)    -> exponent sign, operand transposition, index convention
+  point source                   -> voxel / coil / intensity wiring of Eq. 4
+  adjointness                    -> a missing conjugate or j factor in Eq. 5 vs Eq. 4
+  phase-wrap invariance          -> range handling of large phases
+  dense normal-equation solve    -> the CG recurrence of Fig. 2 Alg. 1 (LAPACK, not CG)
+  Krylov minimisation            -> every early-stopped iterate (the paper stops at 7..56)
+  data-residual monotonicity     -> CG minimises ||E(x - x*)|| over growing Krylov spaces
+  finite differences             -> the B0-map gradient
+  analytic curvature             -> the L-curve corner picker
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_09233_gb300 import synthetic
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _crandn(rng, *shape):
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synthetic.small_2d(seed=11, matrix=12, n_coils=4, n_samples=400, order=3, with_j=True)
+
+
+def test_closed_form_dft_matches_numpy_fft():
+    """Zero B0, no higher orders, Cartesian k-grid: E equals an inverse FFT of S_c*m."""
+    ny, nx, fov_x, fov_y = 6, 10, 0.2, 0.15
+    x, y, _ = synthetic.grid_positions((ny, nx), (fov_x, fov_y))
+    L = nx * ny
+    u = np.arange(nx) - nx // 2
+    w = np.arange(ny) - ny // 2
+    W, U = np.meshgrid(w, u, indexing="ij")
+    kx = 2 * np.pi * U.ravel() / fov_x
+    ky = 2 * np.pi * W.ravel() / fov_y
+    K = kx.shape[0]
+    t = np.arange(K) * 1e-5
+    Km = np.stack([t, kx, ky], axis=1)
+    Rm = np.stack([np.zeros(L), x, y])
+    rng = np.random.default_rng(0)
+    C = 3
+    S = _crandn(rng, L, C)
+    m = _crandn(rng, L)
+    s = oracle.encode(Km, Rm, S, m)
+    for c in range(C):
+        v = (S[:, c] * m).reshape(ny, nx)
+        F = nx * ny * np.fft.ifft2(v)          # sum_v v[iy,ix] e^{+2 pi i (w iy/ny + u ix/nx)}
+        # positions are (i - N/2) d, which multiplies each coefficient by e^{-i pi (u + w)}
+        # for even N; coefficient index (w, u) maps to FFT bin (w mod ny, u mod nx).
+        expect = F[W.ravel() % ny, U.ravel() % nx] * np.exp(-1j * np.pi * (U.ravel() + W.ravel()))
+        assert _rel(s[:, c], expect) < 1e-12
+
+
+def test_point_source_analytic_signal(small):
+    """m = a delta(l0): s(kappa, c) = S(l0, c) j(l0) a exp(i phi(kappa, l0))."""
+    wl = small
+    l0 = 37
+    a = 0.7 - 0.2j
+    m = np.zeros(wl.L, complex)
+    m[l0] = a
+    s = oracle.encode(wl.Kmat, wl.Rmat, wl.S, m, j=wl.j)
+    phi = wl.Kmat @ wl.Rmat[:, l0]
+    expect = np.exp(1j * phi)[:, None] * (wl.S[l0] * wl.j[l0] * a)[None, :]
+    assert _rel(s, expect) < 1e-12
+    # a subset of rows gives the same rows
+    rows = np.array([5, 0, 399, 123])
+    assert _rel(oracle.encode(wl.Kmat, wl.Rmat, wl.S, m, j=wl.j, rows=rows), s[rows]) == 0.0
+
+
+def test_adjointness(small):
+    wl = small
+    rng = np.random.default_rng(1)
+    x = _crandn(rng, wl.L)
+    y = _crandn(rng, wl.K, wl.C)
+    Ex = oracle.encode(wl.Kmat, wl.Rmat, wl.S, x, j=wl.j)
+    EHy = oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y, j=wl.j)
+    lhs = np.vdot(Ex, y)        # <Ex, y>
+    rhs = np.vdot(x, EHy)       # <x, E^H y>
+    assert abs(lhs - rhs) / (np.linalg.norm(Ex) * np.linalg.norm(y)) < 1e-12
+    # voxel subset
+    vox = np.array([3, 140, 0, 77])
+    assert _rel(oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y, j=wl.j, vox=vox), EHy[vox]) == 0.0
+
+
+def test_normal_operator_hermitian_psd(small):
+    wl = small
+    rng = np.random.default_rng(2)
+    u, v = _crandn(rng, wl.L), _crandn(rng, wl.L)
+    Au = oracle.normal(wl.Kmat, wl.Rmat, wl.S, u, j=wl.j)
+    Av = oracle.normal(wl.Kmat, wl.Rmat, wl.S, v, j=wl.j)
+    assert abs(np.vdot(u, Av) - np.vdot(Au, v)) / (np.linalg.norm(Au) * np.linalg.norm(v)) < 1e-12
+    q = np.vdot(v, Av)
+    assert q.real > 0 and abs(q.imag) < 1e-12 * q.real
+
+
+def test_phase_wrap_invariance(small):
+    """Adding 2 pi n / dwell to the B0 map changes every phase by 2 pi n kappa."""
+    wl = small
+    dwell = wl.Kmat[1, 0] - wl.Kmat[0, 0]
+    Km = wl.Kmat.copy()
+    Km[:, 0] = np.arange(wl.K) * dwell  # exact multiples of the dwell
+    rng = np.random.default_rng(3)
+    m = _crandn(rng, wl.L)
+    s0 = oracle.encode(Km, wl.Rmat, wl.S, m, j=wl.j)
+    Rw = wl.Rmat.copy()
+    n = rng.integers(-3, 4, size=wl.L)
+    Rw[0] = Rw[0] + 2 * np.pi * n / dwell
+    s1 = oracle.encode(Km, Rw, wl.S, m, j=wl.j)
+    assert _rel(s1, s0) < 1e-9
+
+
+def _dense_E(wl):
+    cols = []
+    for l in range(wl.L):
+        e = np.zeros(wl.L, complex)
+        e[l] = 1.0
+        cols.append(oracle.encode(wl.Kmat, wl.Rmat, wl.S, e, j=wl.j).ravel())
+    return np.stack(cols, axis=1)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = synthetic.small_2d(seed=21, matrix=6, n_coils=4, n_samples=180, order=2, R=1,
+                            with_j=True)
+    sigma = oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j) + wl.noise
+    return wl, sigma, _dense_E(wl)
+
+
+def test_cg_converges_to_dense_normal_solution(tiny):
+    wl, sigma, E = tiny
+    A = E.conj().T @ E
+    b = E.conj().T @ sigma.ravel()
+    x_star = np.linalg.solve(A, b)
+    out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 4 * wl.L, j=wl.j, apply_j=False)
+    assert _rel(out["x"], x_star) < 1e-9
+    # step 18: the output is multiplied by j
+    out_j = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 4 * wl.L, j=wl.j, apply_j=True)
+    assert _rel(out_j["x"], x_star * wl.j) < 1e-9
+
+
+def test_cg_iterates_minimise_error_over_krylov_space(tiny):
+    """x_n = argmin over K_n(A, b) of ||x - x*||_A: fixes every early-stopped iterate."""
+    wl, sigma, E = tiny
+    A = E.conj().T @ E
+    b = E.conj().T @ sigma.ravel()
+    n_it = 6
+    out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, n_it, j=wl.j, apply_j=False, iterates=True)
+    its = out["iterates"]
+    assert np.all(its[0] == 0)
+    krylov = [b]
+    for n in range(1, n_it + 1):
+        V, _ = np.linalg.qr(np.stack(krylov, axis=1))
+        xn = V @ np.linalg.solve(V.conj().T @ A @ V, V.conj().T @ b)
+        assert _rel(its[n], xn) < 1e-8, n
+        krylov.append(A @ krylov[-1] / np.linalg.norm(A @ krylov[-1]))
+
+
+def test_cg_history_and_residual_monotone(tiny):
+    wl, sigma, E = tiny
+    out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 12, j=wl.j, apply_j=False, history=True,
+                    iterates=True)
+    h = out["history"]
+    b = E.conj().T @ sigma.ravel()
+    assert abs(h[0, 0] - np.linalg.norm(b)) < 1e-12 * np.linalg.norm(b)
+    assert h[0, 1] == 0.0
+    assert abs(h[0, 2] - np.linalg.norm(sigma)) < 1e-12 * np.linalg.norm(sigma)
+    for n in range(h.shape[0]):
+        x = out["iterates"][n]
+        assert abs(h[n, 1] - np.linalg.norm(x)) <= 1e-12 * max(1, np.linalg.norm(x))
+        assert abs(h[n, 2] - np.linalg.norm(E @ x - sigma.ravel())) < 1e-10 * np.linalg.norm(sigma)
+    assert np.all(np.diff(h[:, 2]) <= 1e-12 * h[0, 2])
+    # recursive residual equals the true normal-equation residual b - A x
+    A = E.conj().T @ E
+    for n in (1, 5, 12):
+        x = out["iterates"][n]
+        assert abs(h[n, 0] - np.linalg.norm(b - A @ x)) < 1e-8 * np.linalg.norm(b)
+
+
+def test_cg_relative_tolerance_stop(tiny):
+    wl, sigma, _ = tiny
+    full = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 30, j=wl.j, history=True)
+    tol = 1e-3
+    out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 30, j=wl.j, rel_tol=tol, history=True)
+    r = full["history"][:, 0]
+    first = int(np.argmax(r <= tol * r[0]))
+    assert out["iters"] == first
+    assert _rel(out["x"], oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, first, j=wl.j)["x"]) == 0.0
+
+
+def test_grad_omega_matches_central_differences(small):
+    wl = small
+    rng = np.random.default_rng(4)
+    m = wl.m_true + 0.1 * _crandn(rng, wl.L)
+    d = _crandn(rng, wl.K, wl.C)
+
+    def loss(Rm):
+        r = oracle.encode(wl.Kmat, Rm, wl.S, m, j=wl.j) - d
+        return 0.5 * np.vdot(r, r).real
+
+    g = oracle.encode(wl.Kmat, wl.Rmat, wl.S, m, j=wl.j) - d   # dLoss/dRe + i dLoss/dIm
+    grad = oracle.grad_omega(wl.Kmat, wl.Rmat, wl.S, m, g, j=wl.j)
+    h = 1e-2  # rad/s; phases change by ~t*h <= 2e-5 rad
+    for l in (0, 17, 60, 143):
+        Rp, Rn = wl.Rmat.copy(), wl.Rmat.copy()
+        Rp[0, l] += h
+        Rn[0, l] -= h
+        fd = (loss(Rp) - loss(Rn)) / (2 * h)
+        assert abs(fd - grad[l]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max()), l
+
+
+def test_lcurve_corner_on_parabola_vertex():
+    """(a, b) = (x, x^2) traversed right to left: curvature peaks (value 2) at the vertex."""
+    xs = np.linspace(2.0, -1.0, 31)           # vertex at index 20
+    idx = oracle.lcurve_corner(np.exp(xs), np.exp(xs ** 2))
+    assert idx == 20
+    # a shifted vertex moves the corner with it
+    xs2 = xs + 0.5                             # vertex now where xs == -0.5 -> index 25
+    assert oracle.lcurve_corner(np.exp(xs2), np.exp((xs2 - 0.0) ** 2)) == 25
+    assert oracle.lcurve_corner([1.0, 2.0], [1.0, 1.0]) == -1
