@@ -1,0 +1,292 @@
+"""Benchmark: E^H E applies/s of the CG reconstruction on the 2D 256x256, 32-coil,
+35750-sample (71.5 ms) spiral with 3rd-order field terms.
+
+One step = one sense_cg_solve: b = E^H s, then N_It = 40 CG iterations (each one E^H E
+apply, the vector updates, the history row). value = N_It * steps / time (applies/s,
+summed over ranks); the voxel*sample*coil rate is 2 L K C per apply.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream, with L2 flushed (a 256 MiB write) between steps; barrier + synchronize
+around the timed region, max over ranks. The e2e figure calls the same public entry point
+with HOST buffers (pinned): the H2D copy of Sigma and the D2H copy of the image are inside
+its timed region. Clocks are sampled with nvidia-smi during the timed region.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of the method
+here) on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E^H E applies/s (CG on the normal equations, on-the-fly encoding)"
+UNIT = "applies/s"
+
+
+def _parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tc_fp16", "tc_split"])
+    ap.add_argument("--workload", default="target_256",
+                    choices=["target_256", "precision_128", "plain_32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(name):
+    from paper_2604_09233_gb300 import synthetic
+    return getattr(synthetic, name)()
+
+
+def _config(wl, prec_name):
+    return {"workload": wl.name, "L": wl.L, "K": wl.K, "coils": wl.C, "basis_rows": wl.P1,
+            "cg_iters": wl.n_iter, "precision": prec_name,
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ------------------------------------------------------------------------------------------
+def oracle_apply_rate(wl, budget_s=12.0):
+    """Time the FP64 oracle's E and E^H on a sample of rows/voxels and extrapolate one
+    E^H E apply linearly (both are sums over independent rows / voxels)."""
+    import oracle
+    rng = np.random.default_rng(0)
+    m = wl.m_true
+    y = wl.noise + 1.0
+    n_rows, n_vox = 32, 32
+    t0 = time.perf_counter()
+    oracle.encode(wl.Kmat, wl.Rmat, wl.S, m, j=wl.j, rows=np.arange(n_rows))
+    t_enc = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y, j=wl.j, vox=np.arange(n_vox))
+    t_adj = time.perf_counter() - t0
+    # grow the sample to use the budget
+    scale = max(1.0, (budget_s / 2) / max(t_enc + t_adj, 1e-3))
+    n_rows = int(min(wl.K, n_rows * scale))
+    n_vox = int(min(wl.L, n_vox * scale))
+    rows = np.sort(rng.choice(wl.K, n_rows, replace=False))
+    vox = np.sort(rng.choice(wl.L, n_vox, replace=False))
+    t0 = time.perf_counter()
+    oracle.encode(wl.Kmat, wl.Rmat, wl.S, m, j=wl.j, rows=rows)
+    t_enc = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y, j=wl.j, vox=vox)
+    t_adj = time.perf_counter() - t0
+    t_apply = t_enc * wl.K / n_rows + t_adj * wl.L / n_vox
+    return {"value": 1.0 / t_apply, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"E on {n_rows} of {wl.K} sample rows + E^H on {n_vox} of {wl.L} voxels, "
+                      f"all coils, FP64, extrapolated linearly to one E^H E apply",
+            "seconds": t_enc + t_adj}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = _workload(args.workload)
+    per_step = max(2.0, 100.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_apply_rate(wl, budget_s=per_step)
+    vals, secs = [], 0.0
+    last = None
+    for _ in range(args.steps):
+        last = oracle_apply_rate(wl, budget_s=per_step)
+        vals.append(last["value"])
+        secs += last["seconds"]
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(wl, "fp64 oracle"),
+        "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": value,
+                                                                              "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_09233_gb300 import native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec_name = "fp32" if args.prec == "auto" else args.prec
+    prec = native.PRECISIONS[prec_name]
+
+    wl = _workload(args.workload)
+    plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
+    m = torch.from_numpy(wl.m_true.astype(np.complex64)).to(dev)
+    s = plan.encode(m) + torch.from_numpy(wl.noise.astype(np.complex64)).to(dev)
+    x = torch.empty(wl.L, dtype=torch.complex64, device=dev)
+    n_it = wl.n_iter
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(sv, xv):
+        native.sense_cg_solve(plan.handle, sv, xv, n_it, prec=prec, history=False)
+
+    for _ in range(max(3, args.warmup)):
+        solve(s, x)
+    torch.cuda.synchronize()
+
+    # per-kernel timing of one E^H E apply (device events on the launching stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    flush.fill_(1.0)
+    ev[0].record(stream)
+    native.sense_normal_op(plan.handle, prec, m, x)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_apply_ms = ev[0].elapsed_time(ev[1])
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(float(_))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solve(s, x)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_it * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    s_host = torch.empty((wl.K, wl.C), dtype=torch.complex64).pin_memory()
+    s_host.copy_(s.cpu())
+    x_host = torch.empty(wl.L, dtype=torch.complex64).pin_memory()
+    e2e_t = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        native.sense_cg_solve(plan.handle, s_host.numpy(), x_host.numpy(), n_it, prec=prec,
+                              history=False)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * n_it * len(e2e_t) / float(np.sum(e2e_t))
+
+    vsc = 2.0 * wl.L * wl.K * wl.C
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec_name == "fp32" else "f16",
+        "data": "synthetic", "config": _config(wl, prec_name),
+        "voxel_sample_coil_gops": value * vsc / 1e9,
+        "normal_op_ms": t_apply_ms,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": wl.K * wl.C * 8,
+                "d2h_bytes_per_step": wl.L * 8},
+        "gpu_launches": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_apply_rate(wl)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

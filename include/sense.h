@@ -1,0 +1,151 @@
+/*
+ * sense.h -- C ABI of the GB300 non-Fourier SENSE library (libsense.so).
+ *
+ * The library applies the encoding operator of non-Fourier (higher-order) SENSE and
+ * solves its normal equations by conjugate gradients, with the encoding matrix generated
+ * on the fly on the GPU and never stored.
+ *
+ *   Eq. 4     P = e^{o i K R},  E m == P (S o (m 1^T))           (s = E m, [K][C])
+ *   Eq. 5     E^H sigma == (S* o (P^H Sigma)) 1                   (m = E^H s, [L])
+ *   Fig. 2, Alg. 1 steps 1-18: S <- S o j, CG on E^H E rho = E^H sigma from rho = 0,
+ *             rho <- rho o j.
+ *
+ * Notation (variable table of Fig. 2): L voxels, K samples, C (Gamma) coils, P1 = P + 1
+ * rows of the spatial basis R / columns of the temporal basis K.
+ *
+ * Conventions for every entry point:
+ *  - Return value: SENSE_OK (0) or a negative SENSE_E* code; nothing aborts or throws.
+ *    sense_strerror() names a code; sense_last_error() gives the message of the last
+ *    failing call on the calling thread.
+ *  - Complex arrays are interleaved single precision (re, im) pairs ("complex64").
+ *  - Vector arguments (m, s, x, out) may be DEVICE pointers (the fast path: the call is
+ *    asynchronous on `stream`) or HOST pointers (pageable or pinned: the call stages them
+ *    through plan-owned device buffers and returns after the results are back in host
+ *    memory). The caller owns every buffer it passes; nothing is freed or retained.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - A plan is bound to the device that was current at sense_plan_create(); calls must be
+ *    made with that device current. Calls on one plan must not overlap (they share the
+ *    plan's workspace); different plans are independent.
+ */
+#ifndef SENSE_H
+#define SENSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SENSE_OK 0
+#define SENSE_EINVAL (-1)       /* bad argument: null pointer, size, layout, option  */
+#define SENSE_ENOMEM (-2)       /* device or host allocation failed                  */
+#define SENSE_ECUDA (-3)        /* a CUDA runtime call failed (see sense_last_error) */
+#define SENSE_ENONFINITE (-4)   /* non-finite input, or CG produced a non-finite value */
+#define SENSE_EBREAKDOWN (-5)   /* CG breakdown: p^H E^H E p == 0                    */
+#define SENSE_EUNSUPPORTED (-6) /* valid but unsupported size (e.g. C > 64 coils)    */
+#define SENSE_ENODEVICE (-7)    /* no usable sm_103 device                           */
+
+typedef struct sense_plan_s* sense_plan;
+
+/* Arithmetic used for the two contractions of E and E^H (the phase is always evaluated
+ * the same way, see sense_plan_create). */
+typedef enum {
+  SENSE_PREC_FP32 = 0,     /* FP32 CUDA cores ("explicit" path)                        */
+  SENSE_PREC_TC_FP16 = 1,  /* tcgen05 tensor cores, operands single FP16, FP32 accumulate */
+  SENSE_PREC_TC_SPLIT = 2  /* tcgen05, operands split hi+lo FP16 (3 products), FP32 acc. */
+} sense_precision;
+
+/* Problem definition (Fig. 2 inputs). All pointers are HOST pointers read during
+ * sense_plan_create() only.
+ *   Kmat [K][P1] float64  temporal basis: Kmat[k][0] = t_k (s), Kmat[k][p+1] = k_p(t_k)
+ *   Rmat [P1][L] float64  spatial basis:  Rmat[0][l] = B0(r_l) as angular frequency
+ *                         (rad/s), Rmat[p+1][l] = h_p(r_l); phi = Kmat x Rmat (radians)
+ *   S    [L][C]  complex64 coil sensitivities
+ *   j    [L]     float32 intensity correction, or NULL for all ones                      */
+typedef struct {
+  int64_t L;
+  int64_t K;
+  int32_t C;
+  int32_t P1;
+  const double* Kmat;
+  const double* Rmat;
+  const float* S;
+  const float* j;
+} sense_problem;
+
+/* Create a plan: validates the problem, orders voxels into spatially compact blocks of
+ * 128, derives the per-block phase anchors (FP64 on the device) and uploads S o j.
+ * Phase evaluation: phi/2pi = A(sample block, l) + B(voxel block, k) + sum_q dK(k,q)
+ * dR(l,q), with A and B computed in FP64 and reduced mod 1, and the local bilinear part
+ * in FP32 over the rows of K R that vary inside a block.
+ * Errors: EINVAL (null pointers, L<1, K<1, C<1, P1<1), EUNSUPPORTED (C > 64, more than 20
+ * varying basis rows), ENONFINITE (non-finite Kmat/Rmat/S/j), ENOMEM, ECUDA, ENODEVICE.
+ * On success *out owns device memory until sense_plan_destroy().                        */
+int sense_plan_create(const sense_problem* prob, sense_plan* out);
+
+/* Release every resource of the plan. NULL is accepted. Returns SENSE_OK or ECUDA. */
+int sense_plan_destroy(sense_plan plan);
+
+/* Replace row 0 of R (the B0 map, rad/s, [L] host float64, user voxel order) and rebuild
+ * the phase anchors; used when the B0 map itself is optimised. Errors: EINVAL,
+ * ENONFINITE, ECUDA. Stream-ordered on `stream`. */
+int sense_plan_set_b0(sense_plan plan, const double* omega, void* stream);
+
+/* Plan dimensions: out[0]=L, out[1]=K, out[2]=C, out[3]=P1, out[4]=number of basis rows
+ * kept in the FP32 bilinear part, out[5]=padded L, out[6]=padded K, out[7]=padded C. */
+int sense_plan_info(sense_plan plan, int64_t out[8]);
+
+/* s = E m (Eq. 4). m: [L] complex64, s: [K][C] complex64 (device or host, see above). */
+int sense_encode(sense_plan plan, int prec, const float* m, float* s, void* stream);
+
+/* m = E^H s (Eq. 5). s: [K][C] complex64, m: [L] complex64. */
+int sense_adjoint(sense_plan plan, int prec, const float* s, float* m, void* stream);
+
+/* out = E^H E m (Fig. 2 Alg. 1 step 8). m, out: [L] complex64; may alias. */
+int sense_normal_op(sense_plan plan, int prec, const float* m, float* out, void* stream);
+
+/* CG options. Stopping: the paper's fixed iteration count N_It (max_iter), optionally
+ * also ||r_n|| <= rel_tol ||r_0|| (r_0 = E^H s). */
+typedef struct {
+  int32_t max_iter;     /* N_It >= 0                                                   */
+  int32_t prec;         /* sense_precision of E^H E inside the iterations              */
+  double rel_tol;       /* 0 disables the residual stop                                */
+  int32_t refine_every; /* tensor-core modes: replace the recursive residual by
+                           b - E^H E x with the FP32 operator every this many
+                           iterations (0 = never)                                      */
+  int32_t apply_j;      /* nonzero: multiply the result by j (Alg. 1 step 18)          */
+} sense_cg_opts;
+
+typedef struct {
+  int32_t iters;        /* iterations run                                              */
+  int32_t status;       /* SENSE_OK, SENSE_EBREAKDOWN or SENSE_ENONFINITE              */
+  double rr0;           /* r_0^H r_0                                                   */
+  double rr_final;      /* r_n^H r_n at exit                                           */
+} sense_cg_info;
+
+/* rho = CG(E^H E, E^H s) (Fig. 2 Alg. 1 steps 3-18), starting from rho = 0.
+ *   s        [K][C] complex64 coil data Sigma (device or host)
+ *   x        [L] complex64 output rho (device or host)
+ *   history  NULL or HOST double[(max_iter+1)*3]: for n = 0..iters the row
+ *            (||r_n||, ||rho_n||, ||E rho_n - s||) -- the L-curve coordinates; the data
+ *            residual uses ||E x - s||^2 = ||s||^2 - Re<x,b> - Re<x,r> (r = b - E^H E x)
+ *   info     NULL or HOST output
+ * Returns SENSE_OK when the loop ran (a CG breakdown is reported in info->status, with
+ * rho left at the last finite iterate), or an error code. Synchronises the stream when
+ * history, info or a host x is given. */
+int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opts* opts,
+                   double* history, sense_cg_info* info, void* stream);
+
+/* Maximum-curvature (L-curve corner) index over history rows 1..n-1 of a CG history
+ * (format of sense_cg_solve): points (log ||E x_n - s||, log ||x_n||), curvature signed
+ * positive for the clockwise turn at the corner, central differences; first maximum
+ * wins. Host-only. *corner = -1 when n < 3. Errors: EINVAL. */
+int sense_lcurve_corner(const double* history, int32_t n, int32_t* corner);
+
+const char* sense_strerror(int code);
+const char* sense_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SENSE_H */

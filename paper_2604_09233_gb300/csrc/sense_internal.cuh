@@ -1,0 +1,140 @@
+// Internal declarations shared by the translation units of libsense.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sense.h"
+
+namespace sense {
+
+// Anchor block size: samples are grouped in blocks of TILE consecutive samples, voxels
+// in spatially compact blocks of TILE (k-d order). Every kernel tile lies inside one
+// sample block and one voxel block along each of its two dimensions.
+constexpr int TILE = 128;
+constexpr int MAX_RP = 20;   // max basis rows kept in the FP32 bilinear part
+constexpr int MAX_CP = 64;   // max (padded) coils
+
+// Device scalars of the CG recurrence (double), indices into plan->scal.
+enum ScalarSlot {
+  SC_RR = 0,       // r^H r of the current residual
+  SC_RR0,          // r_0^H r_0
+  SC_PQ_RE,        // p^H q
+  SC_PQ_IM,
+  SC_A_RE,         // alpha / beta of the listing (the step length)
+  SC_A_IM,
+  SC_B_RE,         // ratio for the p update
+  SC_B_IM,
+  SC_SS,           // ||s||^2
+  SC_STOP,         // 0 running, 1 converged (tol), 2 breakdown, 3 non-finite
+  SC_ITER,         // iterations completed
+  SC_TOL2,         // rel_tol^2 * rr0 (0 disables)
+  SC_MAXIT,        // N_It
+  SC_COUNT
+};
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sense
+
+struct sense_plan_s {
+  int device = 0;
+  int num_sms = 0;
+  int64_t L = 0, K = 0;
+  int C = 0, P1 = 0;
+  int64_t Lp = 0, Kp = 0;  // padded to TILE
+  int Cp = 0;              // padded to 8/16/32/64
+  int nsb = 0, nvb = 0;    // sample / voxel blocks
+  int r = 0, RP = 0;       // rows kept in the bilinear part, padded to a multiple of 4
+  std::vector<int> rows;   // which rows of K R vary inside blocks
+
+  // host master geometry
+  std::vector<double> Kh;      // [K][P1]
+  std::vector<double> Rh;      // [P1][L] user order
+  std::vector<float> Sh;       // [L][C] complex interleaved
+  std::vector<float> jh;       // [L] (ones if absent)
+  bool has_j = false;
+  std::vector<int32_t> perm;   // [Lp] plan slot -> user voxel (-1 = padding)
+
+  // device geometry
+  double* dKd = nullptr;     // [Kp][P1]  K / 2pi (turns per unit of R), pad rows = centre
+  double* dRd = nullptr;     // [P1][Lp]  R in plan order, pad = centre
+  double* dKc = nullptr;     // [nsb][P1] sample-block centres (turn units)
+  double* dRc = nullptr;     // [nvb][P1] voxel-block centres
+  int* drows = nullptr;      // [r]
+  int32_t* dperm = nullptr;  // [Lp]
+  float* dK = nullptr;       // [Kp][RP]  (K/2pi - Kc) on kept rows
+  float* dR = nullptr;       // [Lp][RP]  (R - Rc) on kept rows
+  float* Aanc = nullptr;     // [nsb][Lp] frac(Kc . R(l))
+  float* Banc = nullptr;     // [nvb][Kp] frac((K(k) - Kc) . Rc)
+  float2* S = nullptr;       // [Lp][Cp]  S o j, plan order
+  float* jv = nullptr;       // [Lp] j in plan order (1 for padding)
+  float* tk = nullptr;       // [Kp] K(:,0) = t_k as float (0 for padding)
+
+  // FP32 path workspace
+  int nsplit_e = 1, vb_per_split = 1;  // encode: voxel-block split
+  int nsplit_a = 1, sb_per_split = 1;  // adjoint: sample-block split
+  float2* Ypart = nullptr;   // [nsplit_e][Kp][Cp]
+  float2* Y = nullptr;       // [Kp][Cp] operator scratch (E p inside E^H E)
+  float2* Ydata = nullptr;   // [Kp][Cp] coil data Sigma in the internal layout (CG)
+  float2* Xpart = nullptr;   // [nsplit_a][Lp]
+
+  // CG vectors (plan order) and scalars
+  float2 *vx = nullptr, *vr = nullptr, *vp = nullptr, *vq = nullptr, *vb = nullptr,
+         *vm = nullptr;
+  double* scal = nullptr;    // [SC_COUNT]
+  double* hist = nullptr;    // [(max_hist)*3]
+  int max_hist = 0;
+  double* red = nullptr;     // reduction partials
+  unsigned* counter = nullptr;
+  int red_blocks = 0;
+
+  // host staging (for host-pointer arguments)
+  float2* stage_s = nullptr;   // [K][C] device staging for user-layout data
+  float2* stage_m = nullptr;   // [L]    device staging for user-layout images
+};
+
+namespace sense {
+
+// error reporting -------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+#define SENSE_CUDA_TRY(expr)                                   \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return sense::cuda_error(_e, #expr); \
+  } while (0)
+
+bool is_device_pointer(const void* p);
+
+// FP32 CUDA-core operator (sense_fp32.cu) --------------------------------------------
+// All vectors in plan order / internal layouts. The stop flag (nullable) makes the
+// kernels return immediately when nonzero (used inside a converged CG loop).
+int fp32_encode_partials(sense_plan_s* P, const float2* m_plan, const double* stop,
+                         cudaStream_t st);  // -> P->Ypart
+int reduce_y(sense_plan_s* P, float2* Y_int, float2* s_user, const double* stop,
+             cudaStream_t st);             // Ypart -> Y_int [Kp][Cp] and/or s_user [K][C]
+int fp32_adjoint_partials(sense_plan_s* P, const float2* Y_int, const double* stop,
+                          cudaStream_t st);  // -> P->Xpart
+
+// vector kernels (sense_vec.cu) -------------------------------------------------------
+int gather_image(sense_plan_s* P, const float2* m_user, float2* m_plan, cudaStream_t st);
+int scatter_xpart(sense_plan_s* P, float2* m_user, bool apply_j, cudaStream_t st);
+int scatter_image(sense_plan_s* P, const float2* v_plan, float2* m_user, bool apply_j,
+                  cudaStream_t st);
+int load_data(sense_plan_s* P, const float2* s_user, float2* Y_int, cudaStream_t st);
+int reduce_xpart(sense_plan_s* P, float2* q_plan, const double* stop, cudaStream_t st);
+
+// CG (sense_cg.cu) --------------------------------------------------------------------
+int apply_normal_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* q_plan,
+                          const double* stop, cudaStream_t st);
+int adjoint_internal(sense_plan_s* P, int prec, const float2* Y_int, float2* q_plan,
+                     const double* stop, cudaStream_t st);
+
+}  // namespace sense

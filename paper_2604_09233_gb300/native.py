@@ -1,0 +1,259 @@
+"""Thin Python binding of libsense (include/sense.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no arithmetic of
+the method: all of E, E^H, E^H E and CG runs in the CUDA library. Arrays may be torch CUDA
+tensors (device pointers, launched on the current torch stream) or host arrays (numpy /
+CPU tensors; the library stages them). Complex arrays are complex64.
+
+There is no fallback: if libsense.so is missing or fails to load, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsense.so")
+
+SENSE_PREC_FP32 = 0
+SENSE_PREC_TC_FP16 = 1
+SENSE_PREC_TC_SPLIT = 2
+PRECISIONS = {"fp32": SENSE_PREC_FP32, "tc_fp16": SENSE_PREC_TC_FP16,
+              "tc_split": SENSE_PREC_TC_SPLIT}
+
+EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sense_plan_info",
+            "sense_encode", "sense_adjoint", "sense_normal_op", "sense_cg_solve",
+            "sense_lcurve_corner", "sense_strerror", "sense_last_error"]
+
+
+class SenseError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.sense_strerror(code).decode()
+        detail = _lib.sense_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}){': ' + detail if detail else ''}")
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("K", ctypes.c_int64), ("C", ctypes.c_int32),
+                ("P1", ctypes.c_int32), ("Kmat", ctypes.c_void_p), ("Rmat", ctypes.c_void_p),
+                ("S", ctypes.c_void_p), ("j", ctypes.c_void_p)]
+
+
+class CGOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("rel_tol", ctypes.c_double), ("refine_every", ctypes.c_int32),
+                ("apply_j", ctypes.c_int32)]
+
+
+class CGInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rr0", ctypes.c_double), ("rr_final", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsense.so not built ({LIB_PATH}); run paper_2604_09233_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sense_plan_create": ([ctypes.POINTER(_Problem), ctypes.POINTER(vp)], ctypes.c_int),
+        "sense_plan_destroy": ([vp], ctypes.c_int),
+        "sense_plan_set_b0": ([vp, vp, vp], ctypes.c_int),
+        "sense_plan_info": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "sense_encode": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "sense_adjoint": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "sense_normal_op": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "sense_cg_solve": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp, ctypes.POINTER(CGInfo), vp],
+                           ctypes.c_int),
+        "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "sense_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "sense_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SenseError(rc, where)
+
+
+def _ptr(a, dtype=np.complex64):
+    """(pointer, keepalive, stream) for a torch tensor or numpy array (no copies of device data)."""
+    if a is None:
+        return None, None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            want = {np.complex64: torch.complex64, np.float64: torch.float64,
+                    np.float32: torch.float32}[dtype]
+            if a.dtype != want:
+                raise TypeError(f"expected {want}, got {a.dtype}")
+            stream = torch.cuda.current_stream(a.device).cuda_stream if a.is_cuda else None
+            return a.data_ptr(), a, stream
+    except ImportError:
+        pass
+    arr = np.asarray(a)
+    if arr.dtype != dtype or not arr.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+    return arr.ctypes.data, arr, None
+
+
+def _stream(*streams, explicit=None):
+    if explicit is not None:
+        return explicit
+    for s in streams:
+        if s is not None:
+            return s
+    return None
+
+
+def sense_plan_create(Kmat, Rmat, S, j=None):
+    """Create a plan from host arrays Kmat [K][P1], Rmat [P1][L] (float64), S [L][C]
+    (complex64), j [L] (float32 or None). Returns an opaque handle (int)."""
+    Kmat = np.ascontiguousarray(Kmat, np.float64)
+    Rmat = np.ascontiguousarray(Rmat, np.float64)
+    S = np.ascontiguousarray(S, np.complex64)
+    jj = None if j is None else np.ascontiguousarray(j, np.float32)
+    K, P1 = Kmat.shape
+    L = Rmat.shape[1]
+    if Rmat.shape[0] != P1 or S.shape[0] != L or (jj is not None and jj.shape != (L,)):
+        raise ValueError("inconsistent shapes")
+    prob = _Problem(L, K, S.shape[1], P1, Kmat.ctypes.data, Rmat.ctypes.data, S.ctypes.data,
+                    None if jj is None else jj.ctypes.data)
+    h = ctypes.c_void_p()
+    _check(_lib.sense_plan_create(ctypes.byref(prob), ctypes.byref(h)), "sense_plan_create")
+    return h.value
+
+
+def sense_plan_destroy(plan):
+    _check(_lib.sense_plan_destroy(plan), "sense_plan_destroy")
+
+
+def sense_plan_set_b0(plan, omega, stream=None):
+    om = np.ascontiguousarray(omega, np.float64)
+    _check(_lib.sense_plan_set_b0(plan, om.ctypes.data, stream), "sense_plan_set_b0")
+
+
+def sense_plan_info(plan):
+    out = (ctypes.c_int64 * 8)()
+    _check(_lib.sense_plan_info(plan, out), "sense_plan_info")
+    keys = ["L", "K", "C", "P1", "rows_kept", "L_padded", "K_padded", "C_padded"]
+    return dict(zip(keys, list(out)))
+
+
+def sense_encode(plan, prec, m, s, stream=None):
+    pm, km, sm = _ptr(m)
+    ps, ks, ss = _ptr(s)
+    _check(_lib.sense_encode(plan, int(prec), pm, ps, _stream(sm, ss, explicit=stream)),
+           "sense_encode")
+
+
+def sense_adjoint(plan, prec, s, m, stream=None):
+    ps, ks, ss = _ptr(s)
+    pm, km, sm = _ptr(m)
+    _check(_lib.sense_adjoint(plan, int(prec), ps, pm, _stream(ss, sm, explicit=stream)),
+           "sense_adjoint")
+
+
+def sense_normal_op(plan, prec, m, out, stream=None):
+    pm, km, sm = _ptr(m)
+    po, ko, so = _ptr(out)
+    _check(_lib.sense_normal_op(plan, int(prec), pm, po, _stream(sm, so, explicit=stream)),
+           "sense_normal_op")
+
+
+def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refine_every=0,
+                   apply_j=True, history=True, stream=None):
+    """Returns (info dict, history array [iters+1][3] or None)."""
+    ps, ks, ss = _ptr(s)
+    px, kx, sx = _ptr(x)
+    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), int(refine_every),
+                  1 if apply_j else 0)
+    info = CGInfo()
+    hist = np.full((int(max_iter) + 1, 3), np.nan) if history else None
+    _check(_lib.sense_cg_solve(plan, ps, px, ctypes.byref(opts),
+                               None if hist is None else hist.ctypes.data, ctypes.byref(info),
+                               _stream(ss, sx, explicit=stream)), "sense_cg_solve")
+    out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
+    return out, (None if hist is None else hist[: info.iters + 1])
+
+
+def sense_strerror(code):
+    return _lib.sense_strerror(int(code)).decode()
+
+
+def sense_last_error():
+    return _lib.sense_last_error().decode()
+
+
+def sense_lcurve_corner(history):
+    h = np.ascontiguousarray(history, np.float64)
+    c = ctypes.c_int32()
+    _check(_lib.sense_lcurve_corner(h.ctypes.data, int(h.shape[0]), ctypes.byref(c)),
+           "sense_lcurve_corner")
+    return c.value
+
+
+class Plan:
+    """Owns a libsense plan; methods allocate outputs and call the C entry points."""
+
+    def __init__(self, Kmat, Rmat, S, j=None):
+        self.handle = sense_plan_create(Kmat, Rmat, S, j)
+        info = sense_plan_info(self.handle)
+        self.L, self.K, self.C = info["L"], info["K"], info["C"]
+        self.info = info
+
+    def close(self):
+        if self.handle:
+            sense_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def encode(self, m, prec=SENSE_PREC_FP32):
+        import torch
+        s = torch.empty((self.K, self.C), dtype=torch.complex64, device=m.device)
+        sense_encode(self.handle, prec, m, s)
+        return s
+
+    def adjoint(self, s, prec=SENSE_PREC_FP32):
+        import torch
+        m = torch.empty((self.L,), dtype=torch.complex64, device=s.device)
+        sense_adjoint(self.handle, prec, s, m)
+        return m
+
+    def normal(self, m, prec=SENSE_PREC_FP32):
+        import torch
+        out = torch.empty((self.L,), dtype=torch.complex64, device=m.device)
+        sense_normal_op(self.handle, prec, m, out)
+        return out
+
+    def cg(self, s, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refine_every=0, apply_j=True):
+        import torch
+        x = torch.empty((self.L,), dtype=torch.complex64, device=s.device)
+        info, hist = sense_cg_solve(self.handle, s, x, max_iter, prec, rel_tol, refine_every,
+                                    apply_j)
+        return x, info, hist

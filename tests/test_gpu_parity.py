@@ -1,0 +1,197 @@
+"""GPU parity of the FP32 CUDA-core path against the FP64 oracle, through the C ABI.
+
+Bar (FP32 E / E^H): relative L2 error <= 1e-5 versus FP64. CG at equal iteration count:
+<= 1e-4 (single-precision vectors, FP64 scalars). Cases span several 128-wide tiles with
+ragged tails in L, K and C, plus the degenerate shapes (L < 128, K < 128, one coil, the
+64-coil maximum, a B0-only basis).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_09233_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 1e-5
+TOL_CG = 1e-4
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _b0_only(seed=3, L=300, K=700, C=3):
+    rng = np.random.default_rng(seed)
+    t = np.arange(K) * 4e-6
+    Km = t[:, None].copy()
+    Rm = (2 * np.pi * rng.uniform(-200, 200, size=L))[None, :]
+    S = (rng.normal(size=(L, C)) + 1j * rng.normal(size=(L, C))).astype(np.complex64)
+    m = (rng.normal(size=L) + 1j * rng.normal(size=L)).astype(np.complex64)
+    return synthetic.Workload("b0_only", Km, Rm, S.astype(complex), m.astype(complex),
+                              np.zeros((K, C), complex), None, (L,), 5, {})
+
+
+CASES = {
+    "sh3_24x24_c8_k1500_j": lambda: synthetic.small_2d(seed=1, matrix=24, n_coils=8,
+                                                       n_samples=1500, order=3, with_j=True),
+    "lin_20x20_c5_k1000": lambda: synthetic.small_2d(seed=2, matrix=20, n_coils=5,
+                                                     n_samples=1000, order=1),
+    "sh2_16x16_c32_k600": lambda: synthetic.small_2d(seed=3, matrix=16, n_coils=32,
+                                                     n_samples=600, order=2, R=1),
+    "sh3_12x12_c64_k300": lambda: synthetic.small_2d(seed=4, matrix=12, n_coils=64,
+                                                     n_samples=300, order=3, R=1),
+    "tiny_6x6_c1_k100": lambda: synthetic.small_2d(seed=5, matrix=6, n_coils=1, n_samples=100,
+                                                   order=1, R=1),
+    "b0_only_l300_c3": _b0_only,
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    import torch
+    from paper_2604_09233_gb300 import native
+    wl = CASES[request.param]()
+    plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
+    yield wl, plan, torch.device("cuda:0")
+    plan.close()
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.complex64)).to(dev)
+
+
+def test_encode(case):
+    wl, plan, dev = case
+    s = plan.encode(_t(wl.m_true, dev)).cpu().numpy()
+    ref = oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j)
+    assert _rel(s, ref) <= TOL_OP
+
+
+def test_adjoint(case):
+    wl, plan, dev = case
+    rng = np.random.default_rng(9)
+    y = (rng.normal(size=(wl.K, wl.C)) + 1j * rng.normal(size=(wl.K, wl.C))).astype(np.complex64)
+    m = plan.adjoint(_t(y, dev)).cpu().numpy()
+    ref = oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y.astype(complex), j=wl.j)
+    assert _rel(m, ref) <= TOL_OP
+
+
+def test_normal(case):
+    wl, plan, dev = case
+    q = plan.normal(_t(wl.m_true, dev)).cpu().numpy()
+    ref = oracle.normal(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j)
+    assert _rel(q, ref) <= TOL_OP
+
+
+def test_host_pointers_match_device(case):
+    from paper_2604_09233_gb300 import native
+    wl, plan, dev = case
+    m = np.ascontiguousarray(wl.m_true, np.complex64)
+    s_host = np.empty((wl.K, wl.C), np.complex64)
+    native.sense_encode(plan.handle, 0, m, s_host)
+    s_dev = plan.encode(_t(m, dev)).cpu().numpy()
+    assert np.array_equal(s_host, s_dev)
+    m_host = np.empty(wl.L, np.complex64)
+    native.sense_adjoint(plan.handle, 0, s_host, m_host)
+    assert np.array_equal(m_host, plan.adjoint(_t(s_host, dev)).cpu().numpy())
+
+
+def test_cg_equal_iteration_count(case):
+    wl, plan, dev = case
+    sigma = (oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j) + wl.noise).astype(np.complex64)
+    n_it = 10
+    x, info, hist = plan.cg(_t(sigma, dev), n_it)
+    ref = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), n_it, j=wl.j, history=True)
+    assert info["iters"] == n_it and info["status"] == 0
+    assert _rel(x.cpu().numpy(), ref["x"]) <= TOL_CG
+    # history: ||r_n||, ||x_n|| (before j), ||E x_n - s||
+    h, hr = hist, ref["history"]
+    assert np.allclose(h[:, 0], hr[:, 0], rtol=1e-3, atol=1e-6 * hr[0, 0])
+    assert np.allclose(h[:, 2], hr[:, 2], rtol=1e-3, atol=1e-5 * hr[0, 2])
+    if wl.j is None:
+        assert np.allclose(h[:, 1], hr[:, 1], rtol=1e-4, atol=1e-7 * hr[-1, 1])
+
+
+def test_cg_relative_tolerance(case):
+    wl, plan, dev = case
+    sigma = (oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j) + wl.noise).astype(np.complex64)
+    ref = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), 40, j=wl.j, history=True)
+    r = ref["history"][:, 0]
+    tol = float(np.sqrt(r[3] * r[4]) / r[0])       # between iterations 3 and 4
+    x, info, _ = plan.cg(_t(sigma, dev), 40, rel_tol=tol)
+    assert info["iters"] == 4
+    assert _rel(x.cpu().numpy(), oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), 4,
+                                           j=wl.j)["x"]) <= TOL_CG
+
+
+def test_phase_wrap_invariance_and_set_b0():
+    """Large phases that are whole turns change nothing: a global B0 offset of n sampling
+    frequencies (2 pi n / dwell) and a k-space shift of whole grid periods (2 pi n' / dx)
+    add 2 pi * integer to every phase, up to ~2e5 rad here (the anchors reduce mod 2 pi in
+    FP64). set_b0 then follows a new map."""
+    import torch
+    from paper_2604_09233_gb300 import native
+    wl = synthetic.small_2d(seed=6, matrix=20, n_coils=4, n_samples=900, order=3)
+    Km = wl.Kmat.copy()
+    dwell = Km[1, 0]
+    Km[:, 0] = np.arange(wl.K) * dwell
+    dx = wl.meta["fov"] / 20
+    Kw = Km.copy()
+    Kw[:, 2] += 2 * np.pi * 7 / dx          # k_x shifted by 7 grid periods
+    Rw = wl.Rmat.copy()
+    Rw[0] += 2 * np.pi * 61 / dwell          # B0 offset of 61 sampling frequencies
+    dev = torch.device("cuda:0")
+    ref = oracle.encode(Km, wl.Rmat, wl.S, wl.m_true)
+    assert _rel(oracle.encode(Kw, Rw, wl.S, wl.m_true), ref) < 1e-9
+    with native.Plan(Kw, Rw, wl.S) as plan:
+        s = plan.encode(_t(wl.m_true, dev)).cpu().numpy()
+        assert _rel(s, ref) <= TOL_OP
+    with native.Plan(Km, wl.Rmat, wl.S) as plan:
+        om = wl.Rmat[0] * 0.5 + 30.0
+        native.sense_plan_set_b0(plan.handle, om)
+        R2 = wl.Rmat.copy()
+        R2[0] = om
+        s2 = plan.encode(_t(wl.m_true, dev)).cpu().numpy()
+        assert _rel(s2, oracle.encode(Km, R2, wl.S, wl.m_true)) <= TOL_OP
+
+
+@pytest.fixture(scope="module")
+def target():
+    import torch
+    from paper_2604_09233_gb300 import native
+    wl = synthetic.target_256()
+    plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
+    yield wl, plan, torch.device("cuda:0")
+    plan.close()
+
+
+def test_full_size_sampled_rows_and_voxels(target):
+    """2D 256x256, 32 coils, 35750 samples, 3rd-order terms: sampled outputs vs the oracle."""
+    wl, plan, dev = target
+    rng = np.random.default_rng(17)
+    rows = np.sort(rng.choice(wl.K, 48, replace=False))
+    s = plan.encode(_t(wl.m_true, dev)).cpu().numpy()
+    ref = oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, rows=rows)
+    assert _rel(s[rows], ref) <= TOL_OP
+    y = (rng.normal(size=(wl.K, wl.C)) + 1j * rng.normal(size=(wl.K, wl.C))).astype(np.complex64)
+    vox = np.sort(rng.choice(wl.L, 48, replace=False))
+    m = plan.adjoint(_t(y, dev)).cpu().numpy()
+    refm = oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y.astype(complex), vox=vox)
+    assert _rel(m[vox], refm) <= TOL_OP
+
+
+def test_full_size_normal_operator_properties(target):
+    """E^H E is Hermitian and equals E^H (E m) composed from the two entry points."""
+    import torch
+    wl, plan, dev = target
+    rng = np.random.default_rng(5)
+    u = _t(rng.normal(size=wl.L) + 1j * rng.normal(size=wl.L), dev)
+    v = _t(rng.normal(size=wl.L) + 1j * rng.normal(size=wl.L), dev)
+    Au, Av = plan.normal(u), plan.normal(v)
+    lhs = torch.vdot(u, Av).item()
+    rhs = torch.vdot(Au, v).item()
+    assert abs(lhs - rhs) / (torch.linalg.norm(Au).item() * torch.linalg.norm(v).item()) < 1e-5
+    comp = plan.adjoint(plan.encode(u))
+    assert (torch.linalg.norm(comp - Au) / torch.linalg.norm(Au)).item() < 1e-6
