@@ -44,6 +44,7 @@ extern "C" {
 #define SENSE_EBREAKDOWN (-5)   /* CG breakdown: p^H E^H E p == 0                    */
 #define SENSE_EUNSUPPORTED (-6) /* valid but unsupported size (e.g. C > 64 coils)    */
 #define SENSE_ENODEVICE (-7)    /* no usable sm_103 device                           */
+#define SENSE_ETIMEOUT (-8)     /* a tensor-core kernel gave up waiting (bounded wait) */
 
 typedef struct sense_plan_s* sense_plan;
 

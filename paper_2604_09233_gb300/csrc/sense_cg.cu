@@ -306,17 +306,19 @@ int reduce_xpart(sense_plan_s* P, float2* q, const double* stop, cudaStream_t st
 }
 
 static int check_prec(int prec) {
-  if (prec == SENSE_PREC_FP32) return SENSE_OK;
-  if (prec == SENSE_PREC_TC_FP16 || prec == SENSE_PREC_TC_SPLIT)
-    return set_error(SENSE_EUNSUPPORTED, "tensor-core precision modes are not built in");
+  if (prec == SENSE_PREC_FP32 || prec == SENSE_PREC_TC_FP16 || prec == SENSE_PREC_TC_SPLIT)
+    return SENSE_OK;
   return set_error(SENSE_EINVAL, "unknown precision mode");
 }
 
 // q = E^H E p, all in plan order
 int apply_normal_internal(sense_plan_s* P, int prec, const float2* p, float2* q,
                           const double* stop, cudaStream_t st) {
-  (void)prec;
   int rc;
+  if (prec != SENSE_PREC_FP32) {
+    if ((rc = tc_encode(P, prec, p, P->Y, nullptr, true, stop, st)) != SENSE_OK) return rc;
+    return tc_adjoint(P, prec, P->Y, q, true, stop, st);
+  }
   if ((rc = fp32_encode_partials(P, p, stop, st)) != SENSE_OK) return rc;
   if ((rc = reduce_y(P, P->Y, nullptr, stop, st)) != SENSE_OK) return rc;
   if ((rc = fp32_adjoint_partials(P, P->Y, stop, st)) != SENSE_OK) return rc;
@@ -326,8 +328,8 @@ int apply_normal_internal(sense_plan_s* P, int prec, const float2* p, float2* q,
 // q = E^H y for y in the internal data layout
 int adjoint_internal(sense_plan_s* P, int prec, const float2* Y, float2* q, const double* stop,
                      cudaStream_t st) {
-  (void)prec;
   int rc;
+  if (prec != SENSE_PREC_FP32) return tc_adjoint(P, prec, Y, q, false, stop, st);
   if ((rc = fp32_adjoint_partials(P, Y, stop, st)) != SENSE_OK) return rc;
   return reduce_xpart(P, q, stop, st);
 }
@@ -391,9 +393,14 @@ extern "C" int sense_encode(sense_plan P, int prec, const float* m, float* s, vo
   TRY(stage_in(m, P->stage_m, (size_t)P->L * 8, st, &in));
   Staged out = stage_out(s, P->stage_s);
   TRY(gather_image(P, (const float2*)in.dev, P->vm, st));
-  TRY(fp32_encode_partials(P, P->vm, nullptr, st));
-  TRY(reduce_y(P, nullptr, (float2*)out.dev, nullptr, st));
-  return finish_out(out, (size_t)P->K * P->C * 8, st);
+  if (prec == SENSE_PREC_FP32) {
+    TRY(fp32_encode_partials(P, P->vm, nullptr, st));
+    TRY(reduce_y(P, nullptr, (float2*)out.dev, nullptr, st));
+  } else {
+    TRY(tc_encode(P, prec, P->vm, nullptr, (float2*)out.dev, false, nullptr, st));
+  }
+  TRY(finish_out(out, (size_t)P->K * P->C * 8, st));
+  return out.host && prec != SENSE_PREC_FP32 ? tc_check_error(P) : SENSE_OK;
 }
 
 extern "C" int sense_adjoint(sense_plan P, int prec, const float* s, float* m, void* stream) {
@@ -405,9 +412,15 @@ extern "C" int sense_adjoint(sense_plan P, int prec, const float* s, float* m, v
   TRY(stage_in(s, P->stage_s, (size_t)P->K * P->C * 8, st, &in));
   Staged out = stage_out(m, P->stage_m);
   TRY(load_data(P, (const float2*)in.dev, P->Y, st));
-  TRY(fp32_adjoint_partials(P, P->Y, nullptr, st));
-  TRY(scatter_xpart(P, (float2*)out.dev, false, st));
-  return finish_out(out, (size_t)P->L * 8, st);
+  if (prec == SENSE_PREC_FP32) {
+    TRY(fp32_adjoint_partials(P, P->Y, nullptr, st));
+    TRY(scatter_xpart(P, (float2*)out.dev, false, st));
+  } else {
+    TRY(tc_adjoint(P, prec, P->Y, P->vq, false, nullptr, st));
+    TRY(scatter_image(P, P->vq, (float2*)out.dev, false, st));
+  }
+  TRY(finish_out(out, (size_t)P->L * 8, st));
+  return out.host && prec != SENSE_PREC_FP32 ? tc_check_error(P) : SENSE_OK;
 }
 
 extern "C" int sense_normal_op(sense_plan P, int prec, const float* m, float* o, void* stream) {
@@ -421,7 +434,8 @@ extern "C" int sense_normal_op(sense_plan P, int prec, const float* m, float* o,
   Staged out = stage_out(o, P->stage_m);
   TRY(apply_normal_internal(P, prec, P->vm, P->vq, nullptr, st));
   TRY(scatter_image(P, P->vq, (float2*)out.dev, false, st));
-  return finish_out(out, (size_t)P->L * 8, st);
+  TRY(finish_out(out, (size_t)P->L * 8, st));
+  return out.host && prec != SENSE_PREC_FP32 ? tc_check_error(P) : SENSE_OK;
 }
 
 extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sense_cg_opts* opts,
@@ -451,8 +465,10 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   TRY(load_data(P, (const float2*)in.dev, P->Ydata, st));
   data_norm_kernel<<<yb, VB, 0, st>>>(P->Ydata, P->Kp * P->Cp, P->red, P->counter, P->scal);
   SENSE_CUDA_TRY(cudaGetLastError());
-  // step 3: b = E^H sigma (FP32 operator)
-  TRY(adjoint_internal(P, SENSE_PREC_FP32, P->Ydata, P->vb, nullptr, st));
+  // step 3: b = E^H sigma (FP32 operator, or the split tensor-core operator when the
+  // iterations use it)
+  const int prec_b = opts->prec == SENSE_PREC_TC_SPLIT ? SENSE_PREC_TC_SPLIT : SENSE_PREC_FP32;
+  TRY(adjoint_internal(P, prec_b, P->Ydata, P->vb, nullptr, st));
   cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
                                     P->scal, P->hist, opts->rel_tol, N);
   SENSE_CUDA_TRY(cudaGetLastError());
@@ -487,5 +503,7 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
       info->rr_final = sc[SC_RR];
     }
   }
-  return finish_out(out, (size_t)P->L * 8, st);
+  TRY(finish_out(out, (size_t)P->L * 8, st));
+  const bool synced = history || info || out.host;
+  return synced && opts->prec != SENSE_PREC_FP32 ? tc_check_error(P) : SENSE_OK;
 }

@@ -98,6 +98,19 @@ struct sense_plan_s {
   // host staging (for host-pointer arguments)
   float2* stage_s = nullptr;   // [K][C] device staging for user-layout data
   float2* stage_m = nullptr;   // [L]    device staging for user-layout images
+
+  // tensor-core path (sense_tc.cu)
+  int tc_grid = 0;                 // persistent CTAs (one per SM)
+  int tc_slots_e = 1, tc_slots_a = 1;
+  int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E
+  int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [nvb] stream-K slots of E^H
+  uint8_t* Qimg = nullptr;         // B image of S o p   [nvb][2][2][2Cp][128 B]
+  uint8_t* Yimg = nullptr;         // B image of Sigma   [nsb][2][2][2Cp][128 B]
+  float *qscale = nullptr, *yscale = nullptr;  // [Cp] per-coil unscale factors
+  unsigned* colmax = nullptr;      // [2][Cp] per-coil maxima (float bits)
+  float2* Ypart_tc = nullptr;      // [tc_slots_e][Kp][Cp]
+  float2* Xpart_tc = nullptr;      // [tc_slots_a][Lp]
+  int* tc_err = nullptr;           // time-out word written by the tensor-core kernels
 };
 
 namespace sense {
@@ -130,6 +143,17 @@ int scatter_image(sense_plan_s* P, const float2* v_plan, float2* m_user, bool ap
                   cudaStream_t st);
 int load_data(sense_plan_s* P, const float2* s_user, float2* Y_int, cudaStream_t st);
 int reduce_xpart(sense_plan_s* P, float2* q_plan, const double* stop, cudaStream_t st);
+
+// tensor-core operator (sense_tc.cu) ----------------------------------------------------
+int tc_setup(sense_plan_s* P);
+void tc_free(sense_plan_s* P);
+// E p for p in plan order: Y_int [Kp][Cp] and/or s_user [K][C]; want_colmax also records
+// the per-coil maxima of the result for a following tc_adjoint(colmax_ready = true).
+int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, float2* s_user,
+              bool want_colmax, const double* stop, cudaStream_t st);
+int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool colmax_ready,
+               const double* stop, cudaStream_t st);
+int tc_check_error(sense_plan_s* P);
 
 // CG (sense_cg.cu) --------------------------------------------------------------------
 int apply_normal_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* q_plan,

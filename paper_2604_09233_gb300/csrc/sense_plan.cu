@@ -304,6 +304,7 @@ static int alloc_workspace(sense_plan_s* P) {
   SENSE_CUDA_TRY(cudaMemset(P->counter, 0, 4 * sizeof(unsigned)));
   SENSE_TRY(dalloc(&P->stage_s, (size_t)P->K * P->C));
   SENSE_TRY(dalloc(&P->stage_m, (size_t)P->L));
+  SENSE_TRY(tc_setup(P));
   return SENSE_OK;
 }
 
@@ -315,6 +316,7 @@ static void plan_free_all(sense_plan_s* P) {
   cudaFree(P->vx); cudaFree(P->vr); cudaFree(P->vp); cudaFree(P->vq); cudaFree(P->vb);
   cudaFree(P->vm); cudaFree(P->scal); cudaFree(P->hist); cudaFree(P->red);
   cudaFree(P->counter); cudaFree(P->stage_s); cudaFree(P->stage_m);
+  tc_free(P);
   delete P;
 }
 
@@ -439,6 +441,7 @@ extern "C" const char* sense_strerror(int code) {
     case SENSE_EBREAKDOWN: return "CG breakdown";
     case SENSE_EUNSUPPORTED: return "unsupported size";
     case SENSE_ENODEVICE: return "no usable device";
+    case SENSE_ETIMEOUT: return "device wait timed out";
     default: return "unknown error";
   }
 }

@@ -1,0 +1,902 @@
+// Tensor-core (tcgen05) E and E^H with the encoding matrix generated on the fly.
+//
+// One kernel template serves both passes. A pass contracts the phase matrix P = e^{i K R}
+// (Eq. 4) against a thin complex operand over one of its two dimensions:
+//   ENC (s = E m, Eq. 4):    rows = samples, streamed = voxels,  B = Q = S o m
+//   ADJ (m = E^H s, Eq. 5):  rows = voxels,  streamed = samples, B = Sigma,
+//                            generated tile conjugated, coil sum in the epilogue.
+// Per CTA (one per SM, persistent) the warps split into
+//   16 generator warps  : compute 128 rows x 64 streamed phases per stage (FP32 phase,
+//                         MUFU sin/cos), convert to FP16 (hi, or hi+lo split) and write
+//                         them straight into tensor memory as the A operand;
+//   1 MMA warp          : issues tcgen05.mma (A from TMEM, B from shared memory) into two
+//                         FP32 accumulators D1 = A_re B^T, D2 = A_im B^T;
+//   1 loader warp       : bulk-copies (cp.async.bulk) the B tile image, the streamed
+//                         block's phase deltas and its anchors into shared memory.
+// B is the real [2C][64] matrix [B_re; B_im] (per-coil power-of-two scaled FP16, prepared
+// as a pre-swizzled 128B-K-major image), so D1 and D2 give the complex product:
+//   Y_re = D1[:, c] - D2[:, C+c],  Y_im = D1[:, C+c] + D2[:, c].
+// Work is split stream-K: the (row block, streamed block) pairs are cut into equal
+// contiguous ranges, one per CTA; a run of pairs with the same row block accumulates in
+// TMEM and is written to a partial slot, summed in a fixed order afterwards.
+// Every wait is bounded: on time-out the CTA records an error, drains what it issued,
+// frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sense_internal.cuh"
+
+namespace sense {
+namespace tc {
+
+constexpr int NGEN_WARPS = 16;
+constexpr int MMA_WARP = 16;
+constexpr int LOAD_WARP = 17;
+constexpr int NTHREADS = 18 * 32;
+constexpr int NBUF = 2;          // shared-memory stages (one streamed block each)
+constexpr int NSLOT = 2;         // TMEM A slots (one 64-wide half block each)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t A_COL0 = 256;  // first TMEM column of the A slots
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s
+
+enum Mode { ENC = 0, ADJ = 1 };
+
+struct Params {
+  const float* rowD;     // [rows_total][RP]  own-dimension deltas (dK for ENC, dR for ADJ)
+  const float* colD;     // [cols_total][RP]  streamed deltas
+  const float* rowAnc;   // [n_inner][rows_total] (Banc for ENC, Aanc for ADJ)
+  const float* colAnc;   // [n_outer][cols_total] (Aanc for ENC, Banc for ADJ)
+  const uint8_t* Bimg;   // [n_inner][2 halves][NPART][2*CP rows][128 B]
+  const float* bscale;   // [CP] 2^-e unscale per coil
+  const float2* S;       // [rows_total][CP] (ADJ epilogue)
+  float2* out;           // ENC: [slots][rows_total][CP]; ADJ: [slots][rows_total]
+  const int* first_cta;  // [n_outer]
+  int* err;              // device error word (nonzero after a time-out)
+  const double* stop;    // CG stop flag (nullable)
+  long long rows_total, cols_total;
+  long long W;           // n_outer * n_inner
+  int n_outer, n_inner;
+};
+
+// ---------------------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait. Returns false (and raises the CTA abort flag and the global error word)
+// after WAIT_LIMIT_CYCLES, or immediately once another thread has aborted.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       int* err, int site) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0u) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+        *abort_flag = 1;
+        atomicCAS(err, 0, site);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T, kind::f16, M = 128, N from idesc, K = 16
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<2>(uint32_t taddr, float (&v)[2]) {
+  uint32_t r[2];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  for (int i = 0; i < 2; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride-dimension byte offset 1024), descriptor version 1.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// ---------------------------------------------------------------------------------------
+// the pass kernel
+// ---------------------------------------------------------------------------------------
+template <int CP, int NPART>
+struct Smem {
+  static constexpr int BROWS = 2 * CP;
+  static constexpr int B_HALF_BYTES = NPART * BROWS * 128;  // one 64-wide half
+  static constexpr int B_BYTES = 2 * B_HALF_BYTES;           // one streamed block
+};
+
+template <int MODE, int CP, int RP, int NPART>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
+  using SM = Smem<CP, NPART>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-align the dynamic shared memory base
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sB = base;                                              // [NBUF][B_BYTES]
+  float* sCol = (float*)(sB + NBUF * SM::B_BYTES);                 // [NBUF][128][RP]
+  float* sAnc = sCol + NBUF * 128 * RP;                            // [NBUF][128]
+  float2* sRed = (float2*)(sAnc + NBUF * 128);                     // [4][128]
+  uint64_t* bars = (uint64_t*)(sRed + 4 * 128);                    // barriers
+  uint64_t* full = bars;                      // [NBUF]
+  uint64_t* empty = bars + NBUF;              // [NBUF]
+  uint64_t* tfull = bars + 2 * NBUF;          // [NSLOT]
+  uint64_t* tempty = tfull + NSLOT;           // [NSLOT]
+  uint64_t* afull = tempty + NSLOT;           // accumulator full
+  uint64_t* aempty = afull + 1;               // accumulator drained
+  uint64_t* drain = aempty + 1;               // final MMA drain
+  uint64_t* ered = drain + 1;                 // ADJ epilogue: partial sums written
+  uint64_t* edone = ered + 1;                 // ADJ epilogue: partial sums consumed
+  uint32_t* tmem_slot = (uint32_t*)(edone + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (p.stop && *p.stop != 0.0) return;
+
+  const long long G = gridDim.x, i = blockIdx.x;
+  const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(smem_u32(&full[b]), 1);
+      mbar_init(smem_u32(&empty[b]), NGEN_WARPS + 1);
+    }
+    for (int s = 0; s < NSLOT; ++s) {
+      mbar_init(smem_u32(&tfull[s]), NGEN_WARPS);
+      mbar_init(smem_u32(&tempty[s]), 1);
+    }
+    mbar_init(smem_u32(afull), 1);
+    mbar_init(smem_u32(aempty), NGEN_WARPS);
+    mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(ered), NGEN_WARPS);
+    mbar_init(smem_u32(edone), 4);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t D1 = tmem, D2 = tmem + 2 * CP;
+
+  if (warp == LOAD_WARP) {
+    // ------------------------------------------------------------------ loader
+    if (lane == 0) {
+      const uint32_t col_bytes = 128u * RP * 4u;
+      long long it = 0;
+      for (long long w = w0; w < w1; ++w, ++it) {
+        const int o = (int)(w / p.n_inner), in = (int)(w % p.n_inner);
+        const int buf = (int)(it % NBUF);
+        const uint32_t use = (uint32_t)(it / NBUF);
+        if (use > 0 && !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1))
+          break;
+        const uint32_t fb = smem_u32(&full[buf]);
+        mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 512u);
+        bulk_g2s(smem_u32(sB + buf * SM::B_BYTES), p.Bimg + (long long)in * SM::B_BYTES,
+                 SM::B_BYTES, fb);
+        bulk_g2s(smem_u32(sCol + buf * 128 * RP), p.colD + (long long)in * 128 * RP, col_bytes,
+                 fb);
+        bulk_g2s(smem_u32(sAnc + buf * 128), p.colAnc + (long long)o * p.cols_total + in * 128,
+                 512u, fb);
+      }
+      // wait for the last copies this warp issued (one per buffer) before the CTA can exit
+      const long long n = it;
+      for (long long k = (n > NBUF ? n - NBUF : 0); k < n; ++k) {
+        const int buf = (int)(k % NBUF);
+        long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(&full[buf]), (uint32_t)(k / NBUF) & 1u)) {
+          if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+            atomicCAS(p.err, 0, 9);
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(2 * CP);
+      long long it = 0, gstage = 0;
+      int run = 0;
+      bool ok = true;
+      for (long long w = w0; w < w1 && ok; ++w, ++it) {
+        const int buf = (int)(it % NBUF);
+        const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
+        const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
+        if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2)) {
+          ok = false;
+          break;
+        }
+        if (first_in_run && run > 0) {
+          if (!mbar_wait(smem_u32(aempty), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        const uint32_t sbuf = smem_u32(sB + buf * SM::B_BYTES);
+        for (int st = 0; st < 2; ++st, ++gstage) {
+          const int slot = (int)(gstage % NSLOT);
+          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / NSLOT) & 1u, abort_flag, p.err,
+                         4)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acol = tmem + A_COL0 + slot * (NPART * 64);
+          const uint32_t bhi = sbuf + st * SM::B_HALF_BYTES;
+          const uint32_t blo = bhi + 2 * CP * 128;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t acc = (first_in_run && st == 0 && k == 0) ? 0u : 1u;
+            const uint64_t dh = desc_sw128(bhi + 32 * k);
+            if (NPART == 2) {
+              const uint64_t dl = desc_sw128(blo + 32 * k);
+              const uint32_t are_hi = acol + 0 + 8 * k, are_lo = acol + 32 + 8 * k;
+              const uint32_t aim_hi = acol + 64 + 8 * k, aim_lo = acol + 96 + 8 * k;
+              mma_ts(D1, are_hi, dh, idesc, acc);
+              mma_ts(D1, are_hi, dl, idesc, 1u);
+              mma_ts(D1, are_lo, dh, idesc, 1u);
+              mma_ts(D2, aim_hi, dh, idesc, acc);
+              mma_ts(D2, aim_hi, dl, idesc, 1u);
+              mma_ts(D2, aim_lo, dh, idesc, 1u);
+            } else {
+              mma_ts(D1, acol + 8 * k, dh, idesc, acc);
+              mma_ts(D2, acol + 32 + 8 * k, dh, idesc, acc);
+            }
+          }
+          tc_commit(smem_u32(&tempty[slot]));
+        }
+        if (!ok) break;
+        tc_commit(smem_u32(&empty[buf]));
+        if (last_in_run) {
+          tc_commit(smem_u32(afull));
+          ++run;
+        }
+      }
+      // drain every MMA issued before the accumulators / TMEM go away
+      tc_commit(smem_u32(drain));
+      long long t0 = clock64();
+      while (!mbar_try_wait(smem_u32(drain), 0u)) {
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+          atomicCAS(p.err, 0, 10);
+          break;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ generators
+    const int g = warp >> 2;            // warpgroup: K-step of every 64-wide stage
+    const int row = ((warp & 3) << 5) + lane;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    float own[RP];
+    long long it = 0, gstage = 0;
+    int run = 0;
+    bool ok = true;
+    long long cur_o = -1;
+    long long row_g = 0;
+    for (long long w = w0; w < w1 && ok; ++w, ++it) {
+      const int o = (int)(w / p.n_inner), in = (int)(w % p.n_inner);
+      const int buf = (int)(it % NBUF);
+      const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
+      if (o != cur_o) {
+        cur_o = o;
+        row_g = (long long)o * 128 + row;
+#pragma unroll
+        for (int q = 0; q < RP; q += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(p.rowD + row_g * RP + q);
+          own[q] = v.x; own[q + 1] = v.y; own[q + 2] = v.z; own[q + 3] = v.w;
+        }
+      }
+      const float rb = p.rowAnc[(long long)in * p.rows_total + row_g];
+      if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5)) {
+        ok = false;
+        break;
+      }
+      const float* col = sCol + buf * 128 * RP;
+      const float* anc = sAnc + buf * 128;
+      for (int st = 0; st < 2; ++st, ++gstage) {
+        const int slot = (int)(gstage % NSLOT);
+        if (gstage >= NSLOT &&
+            !mbar_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / NSLOT - 1) & 1u, abort_flag,
+                       p.err, 6)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int c0 = st * 64 + g * 16;
+        uint32_t re_hi[8], re_lo[8], im_hi[8], im_lo[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float cs[2], sn[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int v = c0 + 2 * j + h;
+            const float* cv = col + v * RP;
+            float th = 0.0f;
+#pragma unroll
+            for (int q = 0; q < RP; q += 4) {
+              const float4 d = *reinterpret_cast<const float4*>(cv + q);
+              th = fmaf(own[q], d.x, th);
+              th = fmaf(own[q + 1], d.y, th);
+              th = fmaf(own[q + 2], d.z, th);
+              th = fmaf(own[q + 3], d.w, th);
+            }
+            th += anc[v] + rb;
+            th -= rintf(th);
+            __sincosf(6.283185307179586f * th, &sn[h], &cs[h]);
+            if (MODE == ADJ) sn[h] = -sn[h];
+          }
+          re_hi[j] = pack_h2(cs[0], cs[1]);
+          im_hi[j] = pack_h2(sn[0], sn[1]);
+          if (NPART == 2) {
+            const float2 cf = __half22float2(*reinterpret_cast<const __half2*>(&re_hi[j]));
+            const float2 sf = __half22float2(*reinterpret_cast<const __half2*>(&im_hi[j]));
+            re_lo[j] = pack_h2(cs[0] - cf.x, cs[1] - cf.y);
+            im_lo[j] = pack_h2(sn[0] - sf.x, sn[1] - sf.y);
+          }
+        }
+        const uint32_t acol = tmem + lane_base + A_COL0 + slot * (NPART * 64) + g * 8;
+        if (NPART == 2) {
+          tmem_st8(acol + 0, re_hi);
+          tmem_st8(acol + 32, re_lo);
+          tmem_st8(acol + 64, im_hi);
+          tmem_st8(acol + 96, im_lo);
+        } else {
+          tmem_st8(acol + 0, re_hi);
+          tmem_st8(acol + 32, im_hi);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tfull[slot]));
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[buf]));
+
+      if (last_in_run) {
+        // -------------------------------------------------------------- epilogue
+        if (!mbar_wait(smem_u32(afull), (uint32_t)run & 1u, abort_flag, p.err, 7)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        constexpr int CW = CP / 4;  // coils per warpgroup
+        const int cbase = g * CW;
+        float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
+        const uint32_t lb = tmem + lane_base;
+        tmem_ld<CW>(lb + cbase, d1r);               // D1[:, c]      = A_re B_re
+        tmem_ld<CW>(lb + CP + cbase, d1i);          // D1[:, C+c]    = A_re B_im
+        tmem_ld<CW>(lb + 2 * CP + cbase, d2r);      // D2[:, c]      = A_im B_re
+        tmem_ld<CW>(lb + 3 * CP + cbase, d2i);      // D2[:, C+c]    = A_im B_im
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(aempty));
+        const long long slot_o = i - p.first_cta[o];
+        if (MODE == ENC) {
+          float2* dst = p.out + (slot_o * p.rows_total + row_g) * CP + cbase;
+#pragma unroll
+          for (int c = 0; c < CW; ++c) {
+            const float sc = p.bscale[cbase + c];
+            dst[c] = make_float2((d1r[c] - d2i[c]) * sc, (d1i[c] + d2r[c]) * sc);
+          }
+        } else {
+          const float2* Srow = p.S + row_g * CP + cbase;
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < CW; ++c) {
+            const float sc = p.bscale[cbase + c];
+            const float xr = (d1r[c] - d2i[c]) * sc, xi = (d1i[c] + d2r[c]) * sc;
+            const float2 s = Srow[c];
+            acc.x = fmaf(s.x, xr, fmaf(s.y, xi, acc.x));
+            acc.y = fmaf(s.x, xi, fmaf(-s.y, xr, acc.y));
+          }
+          // combine the four warpgroups' coil ranges through shared memory (bounded
+          // mbarrier waits, no unbounded named barrier)
+          if (run > 0 &&
+              !mbar_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8)) {
+            ok = false;
+            break;
+          }
+          sRed[g * 128 + row] = acc;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(ered));
+          if (g == 0) {
+            if (!mbar_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8)) {
+              ok = false;
+              break;
+            }
+            float2 v = sRed[row];
+            for (int k = 1; k < 4; ++k) {
+              v.x += sRed[k * 128 + row].x;
+              v.y += sRed[k * 128 + row].y;
+            }
+            p.out[slot_o * p.rows_total + row_g] = v;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(edone));
+          }
+        }
+        ++run;
+      }
+    }
+    (void)ok;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == MMA_WARP)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+}
+
+template <int CP, int RP, int NPART>
+constexpr size_t smem_bytes() {
+  return 1024 + NBUF * Smem<CP, NPART>::B_BYTES + NBUF * 128 * RP * 4 + NBUF * 128 * 4 +
+         4 * 128 * 8 + 16 * 8 + 16;
+}
+
+// ---------------------------------------------------------------------------------------
+// B-operand images: per-coil power-of-two scaling, FP16 hi (+ lo), 128B-swizzled rows
+// ---------------------------------------------------------------------------------------
+// colmax[c] = max over the block's rows of max(|re|, |im|) of v(r, c) (float bits, >= 0)
+__global__ void colmax_kernel(const float2* __restrict__ src, const float2* __restrict__ S,
+                              const float2* __restrict__ pv, long long nrows, int CP,
+                              unsigned* __restrict__ colmax) {
+  const long long n = nrows * CP;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / CP;
+    const int c = (int)(idx % CP);
+    float2 v;
+    if (src) {
+      v = src[idx];
+    } else {
+      const float2 s = S[idx], m = pv[r];
+      v = make_float2(s.x * m.x - s.y * m.y, s.x * m.y + s.y * m.x);
+    }
+    const float a = fmaxf(fabsf(v.x), fabsf(v.y));
+    if (a > 0.0f) atomicMax(&colmax[c], __float_as_uint(a));
+  }
+}
+
+// One thread per 16-byte chunk (8 consecutive rows r of one image row n, one part).
+template <int NPART>
+__global__ void image_kernel(const float2* __restrict__ src, const float2* __restrict__ S,
+                             const float2* __restrict__ pv, long long nrows, int CP,
+                             const unsigned* __restrict__ colmax, float* __restrict__ bscale,
+                             uint8_t* __restrict__ img) {
+  const int BROWS = 2 * CP;
+  const long long nchunks = (nrows / 8) * BROWS * NPART;
+  if (blockIdx.x == 0 && threadIdx.x < CP) {
+    const float mx = __uint_as_float(colmax[threadIdx.x]);
+    int e = 0;
+    if (mx > 0.0f) frexpf(mx, &e);
+    bscale[threadIdx.x] = mx > 0.0f ? ldexpf(1.0f, e - 15) : 1.0f;
+  }
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nchunks;
+       idx += (long long)gridDim.x * blockDim.x) {
+    // idx -> (row chunk rc = rows rc*8..rc*8+7, image row n, part)
+    const int part = (int)(idx % NPART);
+    const int n = (int)((idx / NPART) % BROWS);
+    const long long rc = idx / (NPART * BROWS);
+    const int c = n % CP;
+    const bool im = n >= CP;
+    const float mx = __uint_as_float(colmax[c]);
+    int e = 0;
+    if (mx > 0.0f) frexpf(mx, &e);
+    const float scale = mx > 0.0f ? ldexpf(1.0f, 15 - e) : 1.0f;
+    uint32_t words[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float vv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long r = rc * 8 + 2 * k + h;
+        float2 v;
+        if (src) {
+          v = src[r * CP + c];
+        } else {
+          const float2 s = S[r * CP + c], m = pv[r];
+          v = make_float2(s.x * m.x - s.y * m.y, s.x * m.y + s.y * m.x);
+        }
+        const float x = (im ? v.y : v.x) * scale;
+        if (part == 0) {
+          vv[h] = x;
+        } else {
+          vv[h] = x - __half2float(__float2half_rn(x));
+        }
+      }
+      words[k] = pack_h2(vv[0], vv[1]);
+    }
+    // placement: block b = r / 128, half = (r % 128) / 64, element e = r % 64
+    const long long r0 = rc * 8;
+    const long long b = r0 / 128;
+    const int half = (int)((r0 % 128) / 64);
+    const int chunk = (int)((r0 % 64) / 8);
+    const long long off = (((b * 2 + half) * NPART + part) * BROWS + n) * 128 +
+                          (long long)((chunk ^ (n & 7)) * 16);
+    *reinterpret_cast<uint4*>(img + off) = make_uint4(words[0], words[1], words[2], words[3]);
+  }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+static int stream_k_layout(long long n_outer, long long n_inner, int G, std::vector<int>& first,
+                           std::vector<int>& nslot, int* max_slots) {
+  const long long W = n_outer * n_inner;
+  auto cta_of = [&](long long w) { return (int)(((w + 1) * G + W - 1) / W - 1); };
+  first.resize(n_outer);
+  nslot.resize(n_outer);
+  int mx = 1;
+  for (long long o = 0; o < n_outer; ++o) {
+    const int a = cta_of(o * n_inner), b = cta_of((o + 1) * n_inner - 1);
+    first[o] = a;
+    nslot[o] = b - a + 1;
+    mx = std::max(mx, b - a + 1);
+  }
+  *max_slots = mx;
+  return SENSE_OK;
+}
+
+template <int MODE, int CP, int RP, int NPART>
+static int launch_pass(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
+  constexpr size_t smem = tc::smem_bytes<CP, RP, NPART>();
+  auto kern = tc::tc_pass_kernel<MODE, CP, RP, NPART>;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    SENSE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    attr_set = true;
+  }
+  kern<<<G, tc::NTHREADS, smem, st>>>(prm);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  return SENSE_OK;
+}
+
+template <int MODE, int CP, int NPART>
+static int dispatch_rp(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
+  switch (P->RP) {
+    case 4: return launch_pass<MODE, CP, 4, NPART>(P, prm, G, st);
+    case 8: return launch_pass<MODE, CP, 8, NPART>(P, prm, G, st);
+    case 12: return launch_pass<MODE, CP, 12, NPART>(P, prm, G, st);
+    case 16: return launch_pass<MODE, CP, 16, NPART>(P, prm, G, st);
+    default: return launch_pass<MODE, CP, 20, NPART>(P, prm, G, st);
+  }
+}
+
+template <int MODE, int NPART>
+static int dispatch_cp(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
+  switch (P->Cp) {
+    case 8: return dispatch_rp<MODE, 8, NPART>(P, prm, G, st);
+    case 16: return dispatch_rp<MODE, 16, NPART>(P, prm, G, st);
+    case 32: return dispatch_rp<MODE, 32, NPART>(P, prm, G, st);
+    default: return dispatch_rp<MODE, 64, NPART>(P, prm, G, st);
+  }
+}
+
+int tc_setup(sense_plan_s* P) {
+  P->tc_grid = P->num_sms;
+  std::vector<int> fe, ne, fa, na;
+  stream_k_layout(P->nsb, P->nvb, P->tc_grid, fe, ne, &P->tc_slots_e);
+  stream_k_layout(P->nvb, P->nsb, P->tc_grid, fa, na, &P->tc_slots_a);
+  auto up = [&](int** d, const std::vector<int>& h) -> int {
+    if (cudaMalloc((void**)d, h.size() * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SENSE_ENOMEM, "tc layout");
+    }
+    SENSE_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return SENSE_OK;
+  };
+  int rc;
+  if ((rc = up(&P->tc_first_e, fe)) != SENSE_OK) return rc;
+  if ((rc = up(&P->tc_nslot_e, ne)) != SENSE_OK) return rc;
+  if ((rc = up(&P->tc_first_a, fa)) != SENSE_OK) return rc;
+  if ((rc = up(&P->tc_nslot_a, na)) != SENSE_OK) return rc;
+  const size_t img_q = (size_t)P->nvb * 2 * 2 * (2 * P->Cp) * 128;   // sized for NPART = 2
+  const size_t img_y = (size_t)P->nsb * 2 * 2 * (2 * P->Cp) * 128;
+  auto al = [&](void** d, size_t bytes) -> int {
+    if (cudaMalloc(d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SENSE_ENOMEM, "tc workspace");
+    }
+    return SENSE_OK;
+  };
+  if ((rc = al((void**)&P->Qimg, img_q)) != SENSE_OK) return rc;
+  if ((rc = al((void**)&P->Yimg, img_y)) != SENSE_OK) return rc;
+  if ((rc = al((void**)&P->qscale, P->Cp * 4)) != SENSE_OK) return rc;
+  if ((rc = al((void**)&P->yscale, P->Cp * 4)) != SENSE_OK) return rc;
+  if ((rc = al((void**)&P->colmax, 2 * P->Cp * 4)) != SENSE_OK) return rc;
+  if ((rc = al((void**)&P->Ypart_tc, (size_t)P->tc_slots_e * P->Kp * P->Cp * 8)) != SENSE_OK)
+    return rc;
+  if ((rc = al((void**)&P->Xpart_tc, (size_t)P->tc_slots_a * P->Lp * 8)) != SENSE_OK) return rc;
+  if ((rc = al((void**)&P->tc_err, 4)) != SENSE_OK) return rc;
+  SENSE_CUDA_TRY(cudaMemset(P->tc_err, 0, 4));
+  return SENSE_OK;
+}
+
+void tc_free(sense_plan_s* P) {
+  cudaFree(P->tc_first_e); cudaFree(P->tc_nslot_e); cudaFree(P->tc_first_a);
+  cudaFree(P->tc_nslot_a); cudaFree(P->Qimg); cudaFree(P->Yimg); cudaFree(P->qscale);
+  cudaFree(P->yscale); cudaFree(P->colmax); cudaFree(P->Ypart_tc); cudaFree(P->Xpart_tc);
+  cudaFree(P->tc_err);
+}
+
+// Y_int[k][c] = sum over the stream-K slots of sample block k/128 (0 for padding);
+// optionally the user-layout copy, and the per-coil maxima for the next image.
+__global__ void tc_reduce_y_kernel(const float2* __restrict__ Ypart, const int* __restrict__ nslot,
+                                   long long K, long long Kp, int C, int Cp,
+                                   float2* __restrict__ Y, float2* __restrict__ su,
+                                   unsigned* __restrict__ colmax, const double* __restrict__ stop) {
+  if (stop && *stop != 0.0) return;
+  const long long n = Kp * Cp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / Cp;
+    const int c = (int)(i % Cp);
+    float2 a = make_float2(0.f, 0.f);
+    if (k < K && c < C) {
+      const int ns = nslot[k / TILE];
+      for (int s = 0; s < ns; ++s) {
+        const float2 v = Ypart[(long long)s * n + i];
+        a.x += v.x;
+        a.y += v.y;
+      }
+    }
+    if (Y) Y[i] = a;
+    if (su && k < K && c < C) su[k * C + c] = a;
+    if (colmax) {
+      const float m = fmaxf(fabsf(a.x), fabsf(a.y));
+      if (m > 0.0f) atomicMax(&colmax[c], __float_as_uint(m));
+    }
+  }
+}
+
+// q[l] = sum over the stream-K slots of voxel block l/128
+__global__ void tc_reduce_x_kernel(const float2* __restrict__ Xpart, const int* __restrict__ nslot,
+                                   long long Lp, float2* __restrict__ q,
+                                   const double* __restrict__ stop) {
+  if (stop && *stop != 0.0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Lp;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ns = nslot[i / TILE];
+    float2 a = make_float2(0.f, 0.f);
+    for (int s = 0; s < ns; ++s) {
+      const float2 v = Xpart[(long long)s * Lp + i];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    q[i] = a;
+  }
+}
+
+static int vgrid(sense_plan_s* P, long long n) {
+  return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8 * P->num_sms));
+}
+
+static int make_image(sense_plan_s* P, int npart, const float2* src, const float2* pv,
+                      long long nrows, unsigned* colmax, float* bscale, uint8_t* img,
+                      bool have_colmax, cudaStream_t st) {
+  if (!have_colmax) {
+    SENSE_CUDA_TRY(cudaMemsetAsync(colmax, 0, P->Cp * 4, st));
+    tc::colmax_kernel<<<vgrid(P, nrows * P->Cp), 256, 0, st>>>(src, P->S, pv, nrows, P->Cp, colmax);
+    SENSE_CUDA_TRY(cudaGetLastError());
+  }
+  const long long nchunks = (nrows / 8) * 2 * P->Cp * npart;
+  if (npart == 2)
+    tc::image_kernel<2><<<vgrid(P, nchunks), 256, 0, st>>>(src, P->S, pv, nrows, P->Cp, colmax,
+                                                           bscale, img);
+  else
+    tc::image_kernel<1><<<vgrid(P, nchunks), 256, 0, st>>>(src, P->S, pv, nrows, P->Cp, colmax,
+                                                           bscale, img);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  return SENSE_OK;
+}
+
+static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, const float* bscale,
+                    float2* out, const double* stop, cudaStream_t st) {
+  tc::Params prm;
+  const bool enc = mode == tc::ENC;
+  prm.rowD = enc ? P->dK : P->dR;
+  prm.colD = enc ? P->dR : P->dK;
+  prm.rowAnc = enc ? P->Banc : P->Aanc;
+  prm.colAnc = enc ? P->Aanc : P->Banc;
+  prm.Bimg = img;
+  prm.bscale = bscale;
+  prm.S = P->S;
+  prm.out = out;
+  prm.first_cta = enc ? P->tc_first_e : P->tc_first_a;
+  prm.err = P->tc_err;
+  prm.stop = stop;
+  prm.rows_total = enc ? P->Kp : P->Lp;
+  prm.cols_total = enc ? P->Lp : P->Kp;
+  prm.n_outer = enc ? P->nsb : P->nvb;
+  prm.n_inner = enc ? P->nvb : P->nsb;
+  prm.W = (long long)prm.n_outer * prm.n_inner;
+  const int G = P->tc_grid;
+  if (enc)
+    return npart == 2 ? dispatch_cp<tc::ENC, 2>(P, prm, G, st) : dispatch_cp<tc::ENC, 1>(P, prm, G, st);
+  return npart == 2 ? dispatch_cp<tc::ADJ, 2>(P, prm, G, st) : dispatch_cp<tc::ADJ, 1>(P, prm, G, st);
+}
+
+static int npart_of(int prec) { return prec == SENSE_PREC_TC_SPLIT ? 2 : 1; }
+
+// Ypart_tc <- E p (p in plan order); then Y_int / s_user / colmax_y as requested
+int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, float2* s_user,
+              bool want_colmax, const double* stop, cudaStream_t st) {
+  const int np = npart_of(prec);
+  int rc;
+  if ((rc = make_image(P, np, nullptr, p_plan, P->Lp, P->colmax, P->qscale, P->Qimg, false, st)))
+    return rc;
+  if ((rc = run_pass(P, tc::ENC, np, P->Qimg, P->qscale, P->Ypart_tc, stop, st))) return rc;
+  unsigned* cm = want_colmax ? P->colmax + P->Cp : nullptr;
+  if (cm) SENSE_CUDA_TRY(cudaMemsetAsync(cm, 0, P->Cp * 4, st));
+  tc_reduce_y_kernel<<<vgrid(P, P->Kp * P->Cp), 256, 0, st>>>(
+      P->Ypart_tc, P->tc_nslot_e, P->K, P->Kp, P->C, P->Cp, Y_int, s_user, cm, stop);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  return SENSE_OK;
+}
+
+// q <- E^H Y_int (plan order). colmax_ready: P->colmax + Cp already holds Y's maxima.
+int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool colmax_ready,
+               const double* stop, cudaStream_t st) {
+  const int np = npart_of(prec);
+  int rc;
+  if ((rc = make_image(P, np, Y_int, nullptr, P->Kp, P->colmax + P->Cp, P->yscale, P->Yimg,
+                       colmax_ready, st)))
+    return rc;
+  if ((rc = run_pass(P, tc::ADJ, np, P->Yimg, P->yscale, P->Xpart_tc, stop, st))) return rc;
+  tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(P->Xpart_tc, P->tc_nslot_a, P->Lp, q, stop);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  return SENSE_OK;
+}
+
+int tc_check_error(sense_plan_s* P) {
+  int e = 0;
+  SENSE_CUDA_TRY(cudaMemcpy(&e, P->tc_err, 4, cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    cudaMemset(P->tc_err, 0, 4);
+    return set_error(SENSE_ETIMEOUT, "tensor-core pass timed out waiting (site " +
+                                         std::to_string(e) + ")");
+  }
+  return SENSE_OK;
+}
+
+}  // namespace sense
