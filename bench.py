@@ -178,6 +178,14 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -190,41 +198,35 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec_name = "fp32" if args.prec == "auto" else args.prec
+    prec_name = "tc_split" if args.prec == "auto" else args.prec
     prec = native.PRECISIONS[prec_name]
 
     wl = _workload(args.workload)
     plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
     m = torch.from_numpy(wl.m_true.astype(np.complex64)).to(dev)
+    # coil data Sigma = E m + noise (E applied by the FP32 path; an input, not a result)
     s = plan.encode(m) + torch.from_numpy(wl.noise.astype(np.complex64)).to(dev)
     x = torch.empty(wl.L, dtype=torch.complex64, device=dev)
     n_it = wl.n_iter
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def solve(sv, xv):
-        native.sense_cg_solve(plan.handle, sv, xv, n_it, prec=prec, history=False)
+    def solve(sv, xv, p=prec):
+        native.sense_cg_solve(plan.handle, sv, xv, n_it, prec=p, history=False)
 
     for _ in range(max(3, args.warmup)):
         solve(s, x)
     torch.cuda.synchronize()
 
-    # per-kernel timing of one E^H E apply (device events on the launching stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    flush.fill_(1.0)
-    ev[0].record(stream)
-    native.sense_normal_op(plan.handle, prec, m, x)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    t_apply_ms = ev[0].elapsed_time(ev[1])
-
+    # ---------------------------------------------------------------- timed region
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    native.sense_plan_profile(plan.handle, True)
     times = []
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(float(_))
+        for i in range(args.steps):
+            flush.fill_(float(i))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             solve(s, x)
@@ -232,6 +234,8 @@ def run_ours(args):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    stats = native.sense_plan_stats(plan.handle)
+    native.sense_plan_profile(plan.handle, False)
     if world > 1:
         dist.barrier()
     total_ms = float(np.sum(times))
@@ -240,8 +244,27 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * n_it * args.steps / (total_ms / 1e3)
+    x_tc = x.clone()
 
-    # end to end through the public API with pinned host buffers
+    # ---------------------------------------------------------------- comparisons (untimed)
+    def apply_rate(p, reps=3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        native.sense_normal_op(plan.handle, p, m, x)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            native.sense_normal_op(plan.handle, p, m, x)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return reps / (ev[0].elapsed_time(ev[1]) / 1e3)
+
+    rates = {name: apply_rate(native.PRECISIONS[name]) for name in ("fp32", "tc_fp16", "tc_split")}
+    x_ref = torch.empty_like(x)
+    native.sense_cg_solve(plan.handle, s, x_ref, n_it, prec=native.SENSE_PREC_FP32, history=False)
+    torch.cuda.synchronize()
+    err_vs_fp32 = (torch.linalg.norm(x_tc - x_ref) / torch.linalg.norm(x_ref)).item()
+
+    # ---------------------------------------------------------------- e2e (host buffers)
     s_host = torch.empty((wl.K, wl.C), dtype=torch.complex64).pin_memory()
     s_host.copy_(s.cpu())
     x_host = torch.empty(wl.L, dtype=torch.complex64).pin_memory()
@@ -256,18 +279,48 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_value = world * n_it * len(e2e_t) / float(np.sum(e2e_t))
 
+    # ---------------------------------------------------------------- roofline
+    # dominant kernel: the tensor-core pass (E or E^H) with the larger share of event time
+    peaks, peak_kind = _peaks()
+    sincos_peak = native.sense_diag_sincos_rate(300.0)
+    info = plan.info
+    Lp, Kp, Cp = info["L_padded"], info["K_padded"], info["C_padded"]
+    kc = "tc_encode_pass" if stats["tc_encode_pass"]["ms"] >= stats["tc_adjoint_pass"]["ms"] \
+        else "tc_adjoint_pass"
+    n_launch = max(1, stats[kc]["n"])
+    t_launch = stats[kc]["ms"] / n_launch / 1e3
+    pairs = float(Lp) * float(Kp)                  # phase pairs generated per launch
+    achieved_sincos = pairs / t_launch
+    mma_per_pair = 6 if prec_name == "tc_split" else 2
+    flops = pairs * mma_per_pair * 2 * (2 * Cp)    # 2 * N per pair per MMA, N = 2 Cp
+    tflops = flops / t_launch / 1e12
+    peak_tc = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    sfu = {"bound": "alu", "achieved": achieved_sincos / 1e9, "peak": sincos_peak / 1e9,
+           "unit": "Gsincos/s", "frac": achieved_sincos / sincos_peak, "traffic": None,
+           "kernel": kc, "per_launch_ms": t_launch * 1e3,
+           "peak_source": "measured on this GPU by sense_diag_sincos_rate"}
+    tensor = {"bound": "tensor", "achieved": tflops, "peak": peak_tc, "unit": "TFLOP/s",
+              "frac": tflops / peak_tc, "traffic": None, "kernel": kc,
+              "peak_source": f"bf16 sustained, {peak_kind} (fp16 = bf16 rate)"}
+    roof = sfu if sfu["frac"] >= tensor["frac"] else tensor
+
     vsc = 2.0 * wl.L * wl.K * wl.C
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec_name == "fp32" else "f16",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16" if prec != 0 else "f32",
         "data": "synthetic", "config": _config(wl, prec_name),
         "voxel_sample_coil_gops": value * vsc / 1e9,
-        "normal_op_ms": t_apply_ms,
+        "applies_per_s_by_precision": rates,
+        "speedup_vs_fp32_path": rates["tc_split"] / rates["fp32"],
+        "cg_rel_err_vs_fp32_path": err_vs_fp32,
+        "roofline": roof,
+        "roofline_other": tensor if roof is sfu else sfu,
+        "kernel_ms": {k: stats[k]["ms"] for k in native.KERNEL_CLASSES},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": wl.K * wl.C * 8,
                 "d2h_bytes_per_step": wl.L * 8},
-        "gpu_launches": None,
+        "gpu_launches": stats["launches"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_apply_rate(wl)

@@ -143,6 +143,28 @@ int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opt
  * wins. Host-only. *corner = -1 when n < 3. Errors: EINVAL. */
 int sense_lcurve_corner(const double* history, int32_t n, int32_t* corner);
 
+/* Diagnostics -------------------------------------------------------------------------
+ * (no counterpart in the paper: measurement support for the kernels above)
+ * Kernel classes: 0 = tensor-core E pass, 1 = tensor-core E^H pass, 2 = FP32 E kernel,
+ * 3 = FP32 E^H kernel. */
+typedef struct {
+  int64_t launches;      /* kernels this plan launched since the last sense_plan_profile() */
+  int64_t timed[4];      /* launches of each class timed with CUDA events (profiling on)   */
+  double ms[4];          /* summed event durations of those launches (ms)                 */
+} sense_stats;
+
+/* Reset the statistics and switch per-launch event timing of the four kernel classes on
+ * (enable != 0) or off. Events are recorded on the stream of each launch. */
+int sense_plan_profile(sense_plan plan, int enable);
+
+/* Read the statistics; waits for the recorded events. Errors: EINVAL, ECUDA. */
+int sense_plan_stats(sense_plan plan, sense_stats* out);
+
+/* Measured sincos throughput of the current device: a kernel that keeps every SM's
+ * special-function unit busy with __sincosf chains; *per_s = sincos evaluations per
+ * second over `ms_budget` milliseconds of work (approximately). Errors: EINVAL, ECUDA. */
+int sense_diag_sincos_rate(double ms_budget, double* per_s);
+
 const char* sense_strerror(int code);
 const char* sense_last_error(void);
 

@@ -276,6 +276,7 @@ static int grid_for(sense_plan_s* P, int64_t n) {
 int gather_image(sense_plan_s* P, const float2* mu, float2* mp, cudaStream_t st) {
   gather_image_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->dperm, mu, mp, P->Lp);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
@@ -283,6 +284,7 @@ int scatter_xpart(sense_plan_s* P, float2* mu, bool apply_j, cudaStream_t st) {
   scatter_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->dperm, P->Xpart, P->nsplit_a, P->Lp, P->jv,
                                                     apply_j ? 1 : 0, mu);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
@@ -290,18 +292,21 @@ int scatter_image(sense_plan_s* P, const float2* vp, float2* mu, bool apply_j, c
   scatter_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->dperm, vp, 1, P->Lp, P->jv,
                                                     apply_j ? 1 : 0, mu);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
 int load_data(sense_plan_s* P, const float2* su, float2* Y, cudaStream_t st) {
   load_data_kernel<<<grid_for(P, P->Kp * P->Cp), VB, 0, st>>>(su, P->K, P->C, P->Kp, P->Cp, Y);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
 int reduce_xpart(sense_plan_s* P, float2* q, const double* stop, cudaStream_t st) {
   reduce_xpart_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->Xpart, P->nsplit_a, P->Lp, q, stop);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
@@ -465,6 +470,7 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   TRY(load_data(P, (const float2*)in.dev, P->Ydata, st));
   data_norm_kernel<<<yb, VB, 0, st>>>(P->Ydata, P->Kp * P->Cp, P->red, P->counter, P->scal);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   // step 3: b = E^H sigma (FP32 operator, or the split tensor-core operator when the
   // iterations use it)
   const int prec_b = opts->prec == SENSE_PREC_TC_SPLIT ? SENSE_PREC_TC_SPLIT : SENSE_PREC_FP32;
@@ -472,17 +478,21 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
                                     P->scal, P->hist, opts->rel_tol, N);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   const double* stop = P->scal + SC_STOP;
   for (int n = 0; n < N; ++n) {
     // step 8
     TRY(apply_normal_internal(P, opts->prec, P->vp, P->vq, stop, st));
     cg_alpha_kernel<<<vb, VB, 0, st>>>(P->vp, P->vq, P->Lp, P->red, P->counter, P->scal);
     SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
     cg_update_kernel<<<vb, VB, 0, st>>>(P->vx, P->vr, P->vp, P->vq, P->vb, P->Lp, P->red,
                                         P->counter, P->scal, P->hist);
     SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
     cg_p_kernel<<<vb, VB, 0, st>>>(P->vp, P->vr, P->Lp, P->scal);
     SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   }
   // step 18
   TRY(scatter_image(P, P->vx, (float2*)out.dev, opts->apply_j != 0, st));

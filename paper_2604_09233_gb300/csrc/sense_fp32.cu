@@ -201,16 +201,22 @@ static void launch_adjoint(sense_plan_s* P, const float2* Y, const double* stop,
 
 int fp32_encode_partials(sense_plan_s* P, const float2* m_plan, const double* stop,
                          cudaStream_t st) {
+  int rc = prof_begin(P, KC_F32_ENC, st);
+  if (rc != SENSE_OK) return rc;
   SENSE_DISPATCH(launch_encode, P, m_plan, stop, st);
   SENSE_CUDA_TRY(cudaGetLastError());
-  return SENSE_OK;
+  count_launch(P);
+  return prof_end(P, st);
 }
 
 int fp32_adjoint_partials(sense_plan_s* P, const float2* Y_int, const double* stop,
                           cudaStream_t st) {
+  int rc = prof_begin(P, KC_F32_ADJ, st);
+  if (rc != SENSE_OK) return rc;
   SENSE_DISPATCH(launch_adjoint, P, Y_int, stop, st);
   SENSE_CUDA_TRY(cudaGetLastError());
-  return SENSE_OK;
+  count_launch(P);
+  return prof_end(P, st);
 }
 
 int reduce_y(sense_plan_s* P, float2* Y_int, float2* s_user, const double* stop,
@@ -220,6 +226,7 @@ int reduce_y(sense_plan_s* P, float2* Y_int, float2* s_user, const double* stop,
   reduce_y_kernel<<<blocks, 256, 0, st>>>(P->Ypart, P->nsplit_e, P->K, P->Kp, P->C, P->Cp,
                                           Y_int, s_user, stop);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 

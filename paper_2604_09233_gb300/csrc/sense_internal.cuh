@@ -111,6 +111,12 @@ struct sense_plan_s {
   float2* Ypart_tc = nullptr;      // [tc_slots_e][Kp][Cp]
   float2* Xpart_tc = nullptr;      // [tc_slots_a][Lp]
   int* tc_err = nullptr;           // time-out word written by the tensor-core kernels
+
+  // diagnostics (sense_diag.cu)
+  int64_t n_launch = 0;
+  bool prof_on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+  size_t prof_used = 0;
 };
 
 namespace sense {
@@ -154,6 +160,15 @@ int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, fl
 int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool colmax_ready,
                const double* stop, cudaStream_t st);
 int tc_check_error(sense_plan_s* P);
+
+// diagnostics (sense_diag.cu) ----------------------------------------------------------
+enum KernelClass { KC_TC_ENC = 0, KC_TC_ADJ = 1, KC_F32_ENC = 2, KC_F32_ADJ = 3 };
+// Bracket one launch of class kc with events on st when profiling is on; call
+// prof_begin before and prof_end after the launch.
+int prof_begin(sense_plan_s* P, int kc, cudaStream_t st);
+int prof_end(sense_plan_s* P, cudaStream_t st);
+void prof_free(sense_plan_s* P);
+inline void count_launch(sense_plan_s* P, int n = 1) { P->n_launch += n; }
 
 // CG (sense_cg.cu) --------------------------------------------------------------------
 int apply_normal_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* q_plan,

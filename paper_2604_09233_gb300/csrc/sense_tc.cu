@@ -686,9 +686,12 @@ static int launch_pass(sense_plan_s* P, const tc::Params& prm, int G, cudaStream
                                         (int)smem));
     attr_set = true;
   }
+  int rc = prof_begin(P, MODE == tc::ENC ? KC_TC_ENC : KC_TC_ADJ, st);
+  if (rc != SENSE_OK) return rc;
   kern<<<G, tc::NTHREADS, smem, st>>>(prm);
   SENSE_CUDA_TRY(cudaGetLastError());
-  return SENSE_OK;
+  count_launch(P);
+  return prof_end(P, st);
 }
 
 template <int MODE, int CP, int NPART>
@@ -818,6 +821,7 @@ static int make_image(sense_plan_s* P, int npart, const float2* src, const float
     SENSE_CUDA_TRY(cudaMemsetAsync(colmax, 0, P->Cp * 4, st));
     tc::colmax_kernel<<<vgrid(P, nrows * P->Cp), 256, 0, st>>>(src, P->S, pv, nrows, P->Cp, colmax);
     SENSE_CUDA_TRY(cudaGetLastError());
+    count_launch(P);
   }
   const long long nchunks = (nrows / 8) * 2 * P->Cp * npart;
   if (npart == 2)
@@ -827,6 +831,7 @@ static int make_image(sense_plan_s* P, int npart, const float2* src, const float
     tc::image_kernel<1><<<vgrid(P, nchunks), 256, 0, st>>>(src, P->S, pv, nrows, P->Cp, colmax,
                                                            bscale, img);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
@@ -871,6 +876,7 @@ int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, fl
   tc_reduce_y_kernel<<<vgrid(P, P->Kp * P->Cp), 256, 0, st>>>(
       P->Ypart_tc, P->tc_nslot_e, P->K, P->Kp, P->C, P->Cp, Y_int, s_user, cm, stop);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 
@@ -885,6 +891,7 @@ int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool c
   if ((rc = run_pass(P, tc::ADJ, np, P->Yimg, P->yscale, P->Xpart_tc, stop, st))) return rc;
   tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(P->Xpart_tc, P->tc_nslot_a, P->Lp, q, stop);
   SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
   return SENSE_OK;
 }
 

@@ -26,7 +26,8 @@ PRECISIONS = {"fp32": SENSE_PREC_FP32, "tc_fp16": SENSE_PREC_TC_FP16,
 
 EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sense_plan_info",
             "sense_encode", "sense_adjoint", "sense_normal_op", "sense_cg_solve",
-            "sense_lcurve_corner", "sense_strerror", "sense_last_error"]
+            "sense_lcurve_corner", "sense_strerror", "sense_last_error", "sense_plan_profile",
+            "sense_plan_stats", "sense_diag_sincos_rate"]
 
 
 class SenseError(RuntimeError):
@@ -35,6 +36,14 @@ class SenseError(RuntimeError):
         msg = _lib.sense_strerror(code).decode()
         detail = _lib.sense_last_error().decode()
         super().__init__(f"{where}: {msg} ({code}){': ' + detail if detail else ''}")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("timed", ctypes.c_int64 * 4),
+                ("ms", ctypes.c_double * 4)]
+
+
+KERNEL_CLASSES = ["tc_encode_pass", "tc_adjoint_pass", "fp32_encode", "fp32_adjoint"]
 
 
 class _Problem(ctypes.Structure):
@@ -70,6 +79,9 @@ def _load():
         "sense_cg_solve": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp, ctypes.POINTER(CGInfo), vp],
                            ctypes.c_int),
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
+        "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "sense_diag_sincos_rate": ([dbl, ctypes.POINTER(dbl)], ctypes.c_int),
         "sense_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sense_last_error": ([], ctypes.c_char_p),
     }
@@ -189,6 +201,27 @@ def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refi
                                _stream(ss, sx, explicit=stream)), "sense_cg_solve")
     out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
     return out, (None if hist is None else hist[: info.iters + 1])
+
+
+def sense_plan_profile(plan, enable=True):
+    _check(_lib.sense_plan_profile(plan, 1 if enable else 0), "sense_plan_profile")
+
+
+def sense_plan_stats(plan):
+    """dict(launches, per-class dict(n=timed launches, ms=summed event time))."""
+    st = Stats()
+    _check(_lib.sense_plan_stats(plan, ctypes.byref(st)), "sense_plan_stats")
+    out = {"launches": st.launches}
+    for i, name in enumerate(KERNEL_CLASSES):
+        out[name] = {"n": st.timed[i], "ms": st.ms[i]}
+    return out
+
+
+def sense_diag_sincos_rate(ms_budget=200.0):
+    v = ctypes.c_double()
+    _check(_lib.sense_diag_sincos_rate(float(ms_budget), ctypes.byref(v)),
+           "sense_diag_sincos_rate")
+    return v.value
 
 
 def sense_strerror(code):
