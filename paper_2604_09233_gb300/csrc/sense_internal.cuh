@@ -71,6 +71,9 @@ struct sense_plan_s {
   int32_t* dperm = nullptr;  // [Lp]
   float* dK = nullptr;       // [Kp][RP]  (K/2pi - Kc) on kept rows
   float* dR = nullptr;       // [Lp][RP]  (R - Rc) on kept rows
+  int RT = 0;                // kept rows padded to the tensor-core kernels' row count
+  float* dKt = nullptr;      // [nsb][RT][TILE] the same deltas, row-major per block
+  float* dRt = nullptr;      // [nvb][RT][TILE]
   float* Aanc = nullptr;     // [nsb][Lp] frac(Kc . R(l))
   float* Banc = nullptr;     // [nvb][Kp] frac((K(k) - Kc) . Rc)
   float2* S = nullptr;       // [Lp][Cp]  S o j, plan order
@@ -101,6 +104,7 @@ struct sense_plan_s {
 
   // tensor-core path (sense_tc.cu)
   int tc_grid = 0;                 // persistent CTAs (one per SM)
+  int tc_seg_len = 8;              // drain the TMEM accumulators every this many pairs
   int tc_slots_e = 1, tc_slots_a = 1;
   int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E
   int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [nvb] stream-K slots of E^H

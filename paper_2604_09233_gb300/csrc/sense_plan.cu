@@ -113,19 +113,26 @@ __global__ void anchors_B_kernel(const double* __restrict__ Kd, const double* __
 __global__ void deltas_kernel(const double* __restrict__ Kd, const double* __restrict__ Kc,
                               const double* __restrict__ Rd, const double* __restrict__ Rc,
                               const int* __restrict__ rows, int r, int RP, int P1, int64_t Kp,
-                              int64_t Lp, float* __restrict__ dK, float* __restrict__ dR) {
+                              int64_t Lp, float* __restrict__ dK, float* __restrict__ dR,
+                              int RT, float* __restrict__ dKt, float* __restrict__ dRt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int RM = RP > RT ? RP : RT;
   if (i < Kp) {
-    const int64_t sb = i / TILE;
-    for (int q = 0; q < RP; ++q)
-      dK[i * RP + q] =
-          q < r ? (float)(Kd[i * P1 + rows[q]] - Kc[sb * P1 + rows[q]]) : 0.0f;
+    const int64_t sb = i / TILE, w = i % TILE;
+    for (int q = 0; q < RM; ++q) {
+      const float v = q < r ? (float)(Kd[i * P1 + rows[q]] - Kc[sb * P1 + rows[q]]) : 0.0f;
+      if (q < RP) dK[i * RP + q] = v;
+      if (q < RT) dKt[(sb * RT + q) * TILE + w] = v;
+    }
   }
   if (i < Lp) {
-    const int64_t vb = i / TILE;
-    for (int q = 0; q < RP; ++q)
-      dR[i * RP + q] =
+    const int64_t vb = i / TILE, w = i % TILE;
+    for (int q = 0; q < RM; ++q) {
+      const float v =
           q < r ? (float)(Rd[(int64_t)rows[q] * Lp + i] - Rc[vb * P1 + rows[q]]) : 0.0f;
+      if (q < RP) dR[i * RP + q] = v;
+      if (q < RT) dRt[(vb * RT + q) * TILE + w] = v;
+    }
   }
 }
 
@@ -149,6 +156,8 @@ static int dalloc(T** p, size_t n) {
 static void free_geometry(sense_plan_s* P) {
   cudaFree(P->dKd); cudaFree(P->dRd); cudaFree(P->dKc); cudaFree(P->dRc);
   cudaFree(P->drows); cudaFree(P->dK); cudaFree(P->dR); cudaFree(P->Aanc); cudaFree(P->Banc);
+  cudaFree(P->dKt); cudaFree(P->dRt);
+  P->dKt = P->dRt = nullptr;
   P->dKd = P->dRd = P->dKc = P->dRc = nullptr;
   P->drows = nullptr;
   P->dK = P->dR = P->Aanc = P->Banc = nullptr;
@@ -215,6 +224,15 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   P->rows = rows;
   P->r = (int)rows.size();
   P->RP = std::max(4, (P->r + 3) / 4 * 4);
+  {
+    static const int rt_sizes[] = {4, 6, 8, 10, 12, 16, 20};
+    P->RT = 20;
+    for (int v : rt_sizes)
+      if (v >= P->r) {
+        P->RT = v;
+        break;
+      }
+  }
 
   free_geometry(P);
   SENSE_TRY(dalloc(&P->dKd, (size_t)Kp * P1));
@@ -224,6 +242,8 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   SENSE_TRY(dalloc(&P->drows, (size_t)std::max(1, P->r)));
   SENSE_TRY(dalloc(&P->dK, (size_t)Kp * P->RP));
   SENSE_TRY(dalloc(&P->dR, (size_t)Lp * P->RP));
+  SENSE_TRY(dalloc(&P->dKt, (size_t)Kp * P->RT));
+  SENSE_TRY(dalloc(&P->dRt, (size_t)Lp * P->RT));
   SENSE_TRY(dalloc(&P->Aanc, (size_t)P->nsb * Lp));
   SENSE_TRY(dalloc(&P->Banc, (size_t)P->nvb * Kp));
   SENSE_CUDA_TRY(cudaMemcpyAsync(P->dKd, Kt.data(), Kt.size() * 8, cudaMemcpyHostToDevice, st));
@@ -241,7 +261,8 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   SENSE_CUDA_TRY(cudaGetLastError());
   const int64_t nmax = std::max(Kp, Lp);
   deltas_kernel<<<(unsigned)((nmax + 255) / 256), 256, 0, st>>>(
-      P->dKd, P->dKc, P->dRd, P->dRc, P->drows, P->r, P->RP, P1, Kp, Lp, P->dK, P->dR);
+      P->dKd, P->dKc, P->dRd, P->dRc, P->drows, P->r, P->RP, P1, Kp, Lp, P->dK, P->dR, P->RT,
+      P->dKt, P->dRt);
   SENSE_CUDA_TRY(cudaGetLastError());
   // the host vectors above die at return: make the copies complete first
   SENSE_CUDA_TRY(cudaStreamSynchronize(st));

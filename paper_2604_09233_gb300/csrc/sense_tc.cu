@@ -44,8 +44,8 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s
 enum Mode { ENC = 0, ADJ = 1 };
 
 struct Params {
-  const float* rowD;     // [rows_total][RP]  own-dimension deltas (dK for ENC, dR for ADJ)
-  const float* colD;     // [cols_total][RP]  streamed deltas
+  const float* rowT;     // [n_outer][RT][128] own-dimension deltas (dK for ENC, dR for ADJ)
+  const float* colT;     // [n_inner][RT][128] streamed deltas
   const float* rowAnc;   // [n_inner][rows_total] (Banc for ENC, Aanc for ADJ)
   const float* colAnc;   // [n_outer][cols_total] (Aanc for ENC, Banc for ADJ)
   const uint8_t* Bimg;   // [n_inner][2 halves][NPART][2*CP rows][128 B]
@@ -58,6 +58,7 @@ struct Params {
   long long rows_total, cols_total;
   long long W;           // n_outer * n_inner
   int n_outer, n_inner;
+  int seg_len;           // accumulator drain interval (pairs of 128 x 128)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -109,6 +110,17 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
       }
     }
   }
+}
+
+// Warp-uniform bounded wait: lane 0 polls, every lane gets the outcome and the warp is
+// converged on return (required before .sync.aligned tcgen05 instructions).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err, int site) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err, site) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
@@ -234,15 +246,17 @@ struct Smem {
   static constexpr int B_BYTES = 2 * B_HALF_BYTES;           // one streamed block
 };
 
-template <int MODE, int CP, int RP, int NPART>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
+template <int MODE, int CP, int RT, int NPART>
+// 576 threads x 112 registers = 64512 of the SM's 65536: one CTA per SM.
+__global__ void __maxnreg__(112) tc_pass_kernel(Params p) {
   using SM = Smem<CP, NPART>;
+  constexpr int CW = CP / 4;  // coils per warpgroup in the epilogue
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-align the dynamic shared memory base
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sB = base;                                              // [NBUF][B_BYTES]
-  float* sCol = (float*)(sB + NBUF * SM::B_BYTES);                 // [NBUF][128][RP]
-  float* sAnc = sCol + NBUF * 128 * RP;                            // [NBUF][128]
+  float* sCol = (float*)(sB + NBUF * SM::B_BYTES);                 // [NBUF][RT][128]
+  float* sAnc = sCol + NBUF * 128 * RT;                            // [NBUF][128]
   float2* sRed = (float2*)(sAnc + NBUF * 128);                     // [4][128]
   uint64_t* bars = (uint64_t*)(sRed + 4 * 128);                    // barriers
   uint64_t* full = bars;                      // [NBUF]
@@ -262,6 +276,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
   const long long G = gridDim.x, i = blockIdx.x;
   const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
+  const int F = p.seg_len;
 
   if (threadIdx.x == 0) {
     for (int b = 0; b < NBUF; ++b) {
@@ -292,10 +307,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t D1 = tmem, D2 = tmem + 2 * CP;
 
+  // A run is a maximal range of pairs with the same row block (one output slot); it is
+  // cut into segments of at most F pairs. After each segment the FP32 accumulators are
+  // read out of TMEM and added to a per-thread running sum in registers (a short
+  // accumulation chain in the tensor core, FP32 adds across segments); the running sum
+  // is written once per run.
+
   if (warp == LOAD_WARP) {
     // ------------------------------------------------------------------ loader
     if (lane == 0) {
-      const uint32_t col_bytes = 128u * RP * 4u;
+      const uint32_t col_bytes = 128u * RT * 4u;
       long long it = 0;
       for (long long w = w0; w < w1; ++w, ++it) {
         const int o = (int)(w / p.n_inner), in = (int)(w % p.n_inner);
@@ -307,7 +328,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 512u);
         bulk_g2s(smem_u32(sB + buf * SM::B_BYTES), p.Bimg + (long long)in * SM::B_BYTES,
                  SM::B_BYTES, fb);
-        bulk_g2s(smem_u32(sCol + buf * 128 * RP), p.colD + (long long)in * 128 * RP, col_bytes,
+        bulk_g2s(smem_u32(sCol + buf * 128 * RT), p.colT + (long long)in * 128 * RT, col_bytes,
                  fb);
         bulk_g2s(smem_u32(sAnc + buf * 128), p.colAnc + (long long)o * p.cols_total + in * 128,
                  512u, fb);
@@ -329,19 +350,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16(2 * CP);
-      long long it = 0, gstage = 0;
-      int run = 0;
+      long long it = 0, gstage = 0, run_start = w0;
+      int seg = 0;
       bool ok = true;
       for (long long w = w0; w < w1 && ok; ++w, ++it) {
         const int buf = (int)(it % NBUF);
         const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
         const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
+        if (first_in_run) run_start = w;
+        const bool seg_first = first_in_run || ((w - run_start) % F == 0);
+        const bool seg_last = last_in_run || ((w - run_start + 1) % F == 0);
         if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2)) {
           ok = false;
           break;
         }
-        if (first_in_run && run > 0) {
-          if (!mbar_wait(smem_u32(aempty), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 3)) {
+        if (seg_first && seg > 0) {
+          if (!mbar_wait(smem_u32(aempty), (uint32_t)(seg - 1) & 1u, abort_flag, p.err, 3)) {
             ok = false;
             break;
           }
@@ -361,7 +385,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           const uint32_t blo = bhi + 2 * CP * 128;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const uint32_t acc = (first_in_run && st == 0 && k == 0) ? 0u : 1u;
+            const uint32_t acc = (seg_first && st == 0 && k == 0) ? 0u : 1u;
             const uint64_t dh = desc_sw128(bhi + 32 * k);
             if (NPART == 2) {
               const uint64_t dl = desc_sw128(blo + 32 * k);
@@ -382,9 +406,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         }
         if (!ok) break;
         tc_commit(smem_u32(&empty[buf]));
-        if (last_in_run) {
+        if (seg_last) {
           tc_commit(smem_u32(afull));
-          ++run;
+          ++seg;
         }
       }
       // drain every MMA issued before the accumulators / TMEM go away
@@ -399,39 +423,56 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     }
   } else {
     // ------------------------------------------------------------------ generators
+    // All waits are warp-uniform (lane 0 polls, the outcome is broadcast) so that every
+    // .sync.aligned tcgen05 instruction below runs with the whole warp converged.
     const int g = warp >> 2;            // warpgroup: K-step of every 64-wide stage
     const int row = ((warp & 3) << 5) + lane;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    float own[RP];
-    long long it = 0, gstage = 0;
-    int run = 0;
+    const int cbase = g * CW;
+    // phase in turns -> radians; the E^H pass generates the conjugate tile
+    const float2 ang_scale = MODE == ADJ ? make_float2(-6.283185307179586f, -6.283185307179586f)
+                                         : make_float2(6.283185307179586f, 6.283185307179586f);
+    const float2 RND = make_float2(12582912.f, 12582912.f);    // 1.5 * 2^23: round to integer
+    const float2 NRND = make_float2(-12582912.f, -12582912.f);
+    const float2 SPL = make_float2(6144.f, 6144.f);            // 1.5 * 2^12: round to 2^-11
+    const float2 NSPL = make_float2(-6144.f, -6144.f);
+    const float2 NEG1 = make_float2(-1.f, -1.f);
+    float own[RT];
+    float2 racc[CW];
+    long long it = 0, gstage = 0, run_start = w0;
+    int seg = 0, run = 0;
     bool ok = true;
     long long cur_o = -1;
     long long row_g = 0;
     for (long long w = w0; w < w1 && ok; ++w, ++it) {
       const int o = (int)(w / p.n_inner), in = (int)(w % p.n_inner);
       const int buf = (int)(it % NBUF);
+      const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
       const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
+      if (first_in_run) {
+        run_start = w;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) racc[c] = make_float2(0.f, 0.f);
+      }
+      const bool seg_last = last_in_run || ((w - run_start + 1) % F == 0);
       if (o != cur_o) {
         cur_o = o;
         row_g = (long long)o * 128 + row;
 #pragma unroll
-        for (int q = 0; q < RP; q += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(p.rowD + row_g * RP + q);
-          own[q] = v.x; own[q + 1] = v.y; own[q + 2] = v.z; own[q + 3] = v.w;
-        }
+        for (int q = 0; q < RT; ++q) own[q] = p.rowT[((long long)o * RT + q) * 128 + row];
       }
       const float rb = p.rowAnc[(long long)in * p.rows_total + row_g];
-      if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5)) {
+      const float2 rb2 = make_float2(rb, rb);
+      if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5)) {
         ok = false;
         break;
       }
-      const float* col = sCol + buf * 128 * RP;
+      const float* col = sCol + buf * 128 * RT;
       const float* anc = sAnc + buf * 128;
       for (int st = 0; st < 2; ++st, ++gstage) {
         const int slot = (int)(gstage % NSLOT);
         if (gstage >= NSLOT &&
-            !mbar_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / NSLOT - 1) & 1u, abort_flag,
+            !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / NSLOT - 1) & 1u, abort_flag,
                        p.err, 6)) {
           ok = false;
           break;
@@ -440,36 +481,53 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         const int c0 = st * 64 + g * 16;
         uint32_t re_hi[8], re_lo[8], im_hi[8], im_lo[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float cs[2], sn[2];
+        for (int jj = 0; jj < 4; ++jj) {
+          const int v0 = c0 + 4 * jj;
+          const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
+          // theta (turns) = A + B + sum_q own_q * delta_q, two pairs per instruction
+          float2 t01 = __fadd2_rn(make_float2(a4.x, a4.y), rb2);
+          float2 t23 = __fadd2_rn(make_float2(a4.z, a4.w), rb2);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int v = c0 + 2 * j + h;
-            const float* cv = col + v * RP;
-            float th = 0.0f;
-#pragma unroll
-            for (int q = 0; q < RP; q += 4) {
-              const float4 d = *reinterpret_cast<const float4*>(cv + q);
-              th = fmaf(own[q], d.x, th);
-              th = fmaf(own[q + 1], d.y, th);
-              th = fmaf(own[q + 2], d.z, th);
-              th = fmaf(own[q + 3], d.w, th);
-            }
-            th += anc[v] + rb;
-            th -= rintf(th);
-            __sincosf(6.283185307179586f * th, &sn[h], &cs[h]);
-            if (MODE == ADJ) sn[h] = -sn[h];
+          for (int q = 0; q < RT; ++q) {
+            const float4 d = *reinterpret_cast<const float4*>(col + q * 128 + v0);
+            const float2 o2 = make_float2(own[q], own[q]);
+            t01 = __ffma2_rn(o2, make_float2(d.x, d.y), t01);
+            t23 = __ffma2_rn(o2, make_float2(d.z, d.w), t23);
           }
-          re_hi[j] = pack_h2(cs[0], cs[1]);
-          im_hi[j] = pack_h2(sn[0], sn[1]);
+          // reduce to [-1/2, 1/2] turn: t - rint(t)
+          t01 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t01, RND), NRND), NEG1, t01);
+          t23 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t23, RND), NRND), NEG1, t23);
+          const float2 a01 = __fmul2_rn(t01, ang_scale), a23 = __fmul2_rn(t23, ang_scale);
+          float2 c01, s01, c23, s23;
+          __sincosf(a01.x, &s01.x, &c01.x);
+          __sincosf(a01.y, &s01.y, &c01.y);
+          __sincosf(a23.x, &s23.x, &c23.x);
+          __sincosf(a23.y, &s23.y, &c23.y);
           if (NPART == 2) {
-            const float2 cf = __half22float2(*reinterpret_cast<const __half2*>(&re_hi[j]));
-            const float2 sf = __half22float2(*reinterpret_cast<const __half2*>(&im_hi[j]));
-            re_lo[j] = pack_h2(cs[0] - cf.x, cs[1] - cf.y);
-            im_lo[j] = pack_h2(sn[0] - sf.x, sn[1] - sf.y);
+            // hi = value rounded to the 2^-11 grid (exact in FP16 for |v| <= 1), lo = rest
+            const float2 hc01 = __fadd2_rn(__fadd2_rn(c01, SPL), NSPL);
+            const float2 hs01 = __fadd2_rn(__fadd2_rn(s01, SPL), NSPL);
+            const float2 hc23 = __fadd2_rn(__fadd2_rn(c23, SPL), NSPL);
+            const float2 hs23 = __fadd2_rn(__fadd2_rn(s23, SPL), NSPL);
+            re_hi[2 * jj] = pack_h2(hc01.x, hc01.y);
+            im_hi[2 * jj] = pack_h2(hs01.x, hs01.y);
+            re_hi[2 * jj + 1] = pack_h2(hc23.x, hc23.y);
+            im_hi[2 * jj + 1] = pack_h2(hs23.x, hs23.y);
+            const float2 lc01 = __ffma2_rn(hc01, NEG1, c01), ls01 = __ffma2_rn(hs01, NEG1, s01);
+            const float2 lc23 = __ffma2_rn(hc23, NEG1, c23), ls23 = __ffma2_rn(hs23, NEG1, s23);
+            re_lo[2 * jj] = pack_h2(lc01.x, lc01.y);
+            im_lo[2 * jj] = pack_h2(ls01.x, ls01.y);
+            re_lo[2 * jj + 1] = pack_h2(lc23.x, lc23.y);
+            im_lo[2 * jj + 1] = pack_h2(ls23.x, ls23.y);
+          } else {
+            re_hi[2 * jj] = pack_h2(c01.x, c01.y);
+            im_hi[2 * jj] = pack_h2(s01.x, s01.y);
+            re_hi[2 * jj + 1] = pack_h2(c23.x, c23.y);
+            im_hi[2 * jj + 1] = pack_h2(s23.x, s23.y);
           }
         }
         const uint32_t acol = tmem + lane_base + A_COL0 + slot * (NPART * 64) + g * 8;
+        __syncwarp();
         if (NPART == 2) {
           tmem_st8(acol + 0, re_hi);
           tmem_st8(acol + 32, re_lo);
@@ -488,15 +546,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[buf]));
 
-      if (last_in_run) {
-        // -------------------------------------------------------------- epilogue
-        if (!mbar_wait(smem_u32(afull), (uint32_t)run & 1u, abort_flag, p.err, 7)) {
+      if (seg_last) {
+        // ------------------------------------------------ segment drain into registers
+        if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        constexpr int CW = CP / 4;  // coils per warpgroup
-        const int cbase = g * CW;
         float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
         const uint32_t lb = tmem + lane_base;
         tmem_ld<CW>(lb + cbase, d1r);               // D1[:, c]      = A_re B_re
@@ -506,13 +562,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(aempty));
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          racc[c].x += d1r[c] - d2i[c];
+          racc[c].y += d1i[c] + d2r[c];
+        }
+        ++seg;
+      }
+      if (last_in_run) {
+        // ------------------------------------------------ run output
         const long long slot_o = i - p.first_cta[o];
         if (MODE == ENC) {
           float2* dst = p.out + (slot_o * p.rows_total + row_g) * CP + cbase;
 #pragma unroll
           for (int c = 0; c < CW; ++c) {
             const float sc = p.bscale[cbase + c];
-            dst[c] = make_float2((d1r[c] - d2i[c]) * sc, (d1i[c] + d2r[c]) * sc);
+            dst[c] = make_float2(racc[c].x * sc, racc[c].y * sc);
           }
         } else {
           const float2* Srow = p.S + row_g * CP + cbase;
@@ -520,7 +585,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 #pragma unroll
           for (int c = 0; c < CW; ++c) {
             const float sc = p.bscale[cbase + c];
-            const float xr = (d1r[c] - d2i[c]) * sc, xi = (d1i[c] + d2r[c]) * sc;
+            const float xr = racc[c].x * sc, xi = racc[c].y * sc;
             const float2 s = Srow[c];
             acc.x = fmaf(s.x, xr, fmaf(s.y, xi, acc.x));
             acc.y = fmaf(s.x, xi, fmaf(-s.y, xr, acc.y));
@@ -528,7 +593,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           // combine the four warpgroups' coil ranges through shared memory (bounded
           // mbarrier waits, no unbounded named barrier)
           if (run > 0 &&
-              !mbar_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8)) {
+              !warp_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8)) {
             ok = false;
             break;
           }
@@ -536,7 +601,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(ered));
           if (g == 0) {
-            if (!mbar_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8)) {
+            if (!warp_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8)) {
               ok = false;
               break;
             }
@@ -559,9 +624,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == MMA_WARP)
+  if (warp == MMA_WARP) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS));
+  }
 }
 
 template <int CP, int RP, int NPART>
@@ -696,9 +763,11 @@ static int launch_pass(sense_plan_s* P, const tc::Params& prm, int G, cudaStream
 
 template <int MODE, int CP, int NPART>
 static int dispatch_rp(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
-  switch (P->RP) {
+  switch (P->RT) {
     case 4: return launch_pass<MODE, CP, 4, NPART>(P, prm, G, st);
+    case 6: return launch_pass<MODE, CP, 6, NPART>(P, prm, G, st);
     case 8: return launch_pass<MODE, CP, 8, NPART>(P, prm, G, st);
+    case 10: return launch_pass<MODE, CP, 10, NPART>(P, prm, G, st);
     case 12: return launch_pass<MODE, CP, 12, NPART>(P, prm, G, st);
     case 16: return launch_pass<MODE, CP, 16, NPART>(P, prm, G, st);
     default: return launch_pass<MODE, CP, 20, NPART>(P, prm, G, st);
@@ -839,8 +908,8 @@ static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, co
                     float2* out, const double* stop, cudaStream_t st) {
   tc::Params prm;
   const bool enc = mode == tc::ENC;
-  prm.rowD = enc ? P->dK : P->dR;
-  prm.colD = enc ? P->dR : P->dK;
+  prm.rowT = enc ? P->dKt : P->dRt;
+  prm.colT = enc ? P->dRt : P->dKt;
   prm.rowAnc = enc ? P->Banc : P->Aanc;
   prm.colAnc = enc ? P->Aanc : P->Banc;
   prm.Bimg = img;
@@ -855,6 +924,7 @@ static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, co
   prm.n_outer = enc ? P->nsb : P->nvb;
   prm.n_inner = enc ? P->nvb : P->nsb;
   prm.W = (long long)prm.n_outer * prm.n_inner;
+  prm.seg_len = P->tc_seg_len;
   const int G = P->tc_grid;
   if (enc)
     return npart == 2 ? dispatch_cp<tc::ENC, 2>(P, prm, G, st) : dispatch_cp<tc::ENC, 1>(P, prm, G, st);
