@@ -43,7 +43,34 @@ def _parse():
     ap.add_argument("--workload", default="target_256",
                     choices=["target_256", "precision_128", "plain_32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op-only", action="store_true",
+                    help="time only W + K single E^H E applies (used for kernel profiling)")
     return ap.parse_args()
+
+
+def run_op_only(args):
+    """W warm-up and K timed sense_normal_op calls; prints one JSON line. The tensor-core
+    E and E^H passes are the 2nd..(2K+1)th kernels after the warm-up ones."""
+    import torch
+    from paper_2604_09233_gb300 import native
+    prec_name = "tc_split" if args.prec == "auto" else args.prec
+    prec = native.PRECISIONS[prec_name]
+    wl = _workload(args.workload)
+    dev = torch.device("cuda", 0)
+    plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
+    m = torch.from_numpy(wl.m_true.astype(np.complex64)).to(dev)
+    out = torch.empty_like(m)
+    for _ in range(args.warmup):
+        native.sense_normal_op(plan.handle, prec, m, out)
+    torch.cuda.synchronize()
+    native.sense_plan_profile(plan.handle, True)
+    for _ in range(args.steps):
+        native.sense_normal_op(plan.handle, prec, m, out)
+    torch.cuda.synchronize()
+    st = native.sense_plan_stats(plan.handle)
+    print(json.dumps({"op_only": True, "workload": wl.name, "precision": prec_name,
+                      "steps": args.steps, "stats": st}), flush=True)
+    plan.close()
 
 
 def _workload(name):
@@ -337,6 +364,8 @@ def main():
     args = _parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.op_only:
+        run_op_only(args)
     else:
         run_ours(args)
 
