@@ -163,6 +163,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -247,8 +253,9 @@ struct Smem {
 };
 
 template <int MODE, int CP, int RT, int NPART>
-// 576 threads x 112 registers = 64512 of the SM's 65536: one CTA per SM.
-__global__ void __maxnreg__(112) tc_pass_kernel(Params p) {
+// 18 warps: up to 5 on one SM sub-partition, whose register file holds 16K registers, so
+// 96 registers per thread is the ceiling; one CTA per SM.
+__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   using SM = Smem<CP, NPART>;
   constexpr int CW = CP / 4;  // coils per warpgroup in the epilogue
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -479,63 +486,68 @@ __global__ void __maxnreg__(112) tc_pass_kernel(Params p) {
         }
         tc_fence_after();
         const int c0 = st * 64 + g * 16;
-        uint32_t re_hi[8], re_lo[8], im_hi[8], im_lo[8];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int v0 = c0 + 4 * jj;
-          const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
-          // theta (turns) = A + B + sum_q own_q * delta_q, two pairs per instruction
-          float2 t01 = __fadd2_rn(make_float2(a4.x, a4.y), rb2);
-          float2 t23 = __fadd2_rn(make_float2(a4.z, a4.w), rb2);
-#pragma unroll
-          for (int q = 0; q < RT; ++q) {
-            const float4 d = *reinterpret_cast<const float4*>(col + q * 128 + v0);
-            const float2 o2 = make_float2(own[q], own[q]);
-            t01 = __ffma2_rn(o2, make_float2(d.x, d.y), t01);
-            t23 = __ffma2_rn(o2, make_float2(d.z, d.w), t23);
-          }
-          // reduce to [-1/2, 1/2] turn: t - rint(t)
-          t01 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t01, RND), NRND), NEG1, t01);
-          t23 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t23, RND), NRND), NEG1, t23);
-          const float2 a01 = __fmul2_rn(t01, ang_scale), a23 = __fmul2_rn(t23, ang_scale);
-          float2 c01, s01, c23, s23;
-          __sincosf(a01.x, &s01.x, &c01.x);
-          __sincosf(a01.y, &s01.y, &c01.y);
-          __sincosf(a23.x, &s23.x, &c23.x);
-          __sincosf(a23.y, &s23.y, &c23.y);
-          if (NPART == 2) {
-            // hi = value rounded to the 2^-11 grid (exact in FP16 for |v| <= 1), lo = rest
-            const float2 hc01 = __fadd2_rn(__fadd2_rn(c01, SPL), NSPL);
-            const float2 hs01 = __fadd2_rn(__fadd2_rn(s01, SPL), NSPL);
-            const float2 hc23 = __fadd2_rn(__fadd2_rn(c23, SPL), NSPL);
-            const float2 hs23 = __fadd2_rn(__fadd2_rn(s23, SPL), NSPL);
-            re_hi[2 * jj] = pack_h2(hc01.x, hc01.y);
-            im_hi[2 * jj] = pack_h2(hs01.x, hs01.y);
-            re_hi[2 * jj + 1] = pack_h2(hc23.x, hc23.y);
-            im_hi[2 * jj + 1] = pack_h2(hs23.x, hs23.y);
-            const float2 lc01 = __ffma2_rn(hc01, NEG1, c01), ls01 = __ffma2_rn(hs01, NEG1, s01);
-            const float2 lc23 = __ffma2_rn(hc23, NEG1, c23), ls23 = __ffma2_rn(hs23, NEG1, s23);
-            re_lo[2 * jj] = pack_h2(lc01.x, lc01.y);
-            im_lo[2 * jj] = pack_h2(ls01.x, ls01.y);
-            re_lo[2 * jj + 1] = pack_h2(lc23.x, lc23.y);
-            im_lo[2 * jj + 1] = pack_h2(ls23.x, ls23.y);
-          } else {
-            re_hi[2 * jj] = pack_h2(c01.x, c01.y);
-            im_hi[2 * jj] = pack_h2(s01.x, s01.y);
-            re_hi[2 * jj + 1] = pack_h2(c23.x, c23.y);
-            im_hi[2 * jj + 1] = pack_h2(s23.x, s23.y);
-          }
-        }
         const uint32_t acol = tmem + lane_base + A_COL0 + slot * (NPART * 64) + g * 8;
-        __syncwarp();
-        if (NPART == 2) {
-          tmem_st8(acol + 0, re_hi);
-          tmem_st8(acol + 32, re_lo);
-          tmem_st8(acol + 64, im_hi);
-          tmem_st8(acol + 96, im_lo);
-        } else {
-          tmem_st8(acol + 0, re_hi);
-          tmem_st8(acol + 32, im_hi);
+        // two halves of 8 streamed elements (4 TMEM columns per matrix each)
+#pragma unroll
+        for (int jh = 0; jh < 2; ++jh) {
+          uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+#pragma unroll
+          for (int j2 = 0; j2 < 2; ++j2) {
+            const int v0 = c0 + 8 * jh + 4 * j2;
+            const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
+            // theta (turns) = A + B + sum_q own_q * delta_q, two pairs per instruction
+            float2 t01 = __fadd2_rn(make_float2(a4.x, a4.y), rb2);
+            float2 t23 = __fadd2_rn(make_float2(a4.z, a4.w), rb2);
+#pragma unroll
+            for (int q = 0; q < RT; ++q) {
+              const float4 d = *reinterpret_cast<const float4*>(col + q * 128 + v0);
+              const float2 o2 = make_float2(own[q], own[q]);
+              t01 = __ffma2_rn(o2, make_float2(d.x, d.y), t01);
+              t23 = __ffma2_rn(o2, make_float2(d.z, d.w), t23);
+            }
+            // reduce to [-1/2, 1/2] turn: t - rint(t)
+            t01 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t01, RND), NRND), NEG1, t01);
+            t23 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t23, RND), NRND), NEG1, t23);
+            const float2 a01 = __fmul2_rn(t01, ang_scale), a23 = __fmul2_rn(t23, ang_scale);
+            float2 c01, s01, c23, s23;
+            __sincosf(a01.x, &s01.x, &c01.x);
+            __sincosf(a01.y, &s01.y, &c01.y);
+            __sincosf(a23.x, &s23.x, &c23.x);
+            __sincosf(a23.y, &s23.y, &c23.y);
+            if (NPART == 2) {
+              // hi = value rounded to the 2^-11 grid (exact in FP16 for |v| <= 1), lo = rest
+              const float2 hc01 = __fadd2_rn(__fadd2_rn(c01, SPL), NSPL);
+              const float2 hs01 = __fadd2_rn(__fadd2_rn(s01, SPL), NSPL);
+              const float2 hc23 = __fadd2_rn(__fadd2_rn(c23, SPL), NSPL);
+              const float2 hs23 = __fadd2_rn(__fadd2_rn(s23, SPL), NSPL);
+              re_hi[2 * j2] = pack_h2(hc01.x, hc01.y);
+              im_hi[2 * j2] = pack_h2(hs01.x, hs01.y);
+              re_hi[2 * j2 + 1] = pack_h2(hc23.x, hc23.y);
+              im_hi[2 * j2 + 1] = pack_h2(hs23.x, hs23.y);
+              const float2 lc01 = __ffma2_rn(hc01, NEG1, c01), ls01 = __ffma2_rn(hs01, NEG1, s01);
+              const float2 lc23 = __ffma2_rn(hc23, NEG1, c23), ls23 = __ffma2_rn(hs23, NEG1, s23);
+              re_lo[2 * j2] = pack_h2(lc01.x, lc01.y);
+              im_lo[2 * j2] = pack_h2(ls01.x, ls01.y);
+              re_lo[2 * j2 + 1] = pack_h2(lc23.x, lc23.y);
+              im_lo[2 * j2 + 1] = pack_h2(ls23.x, ls23.y);
+            } else {
+              re_hi[2 * j2] = pack_h2(c01.x, c01.y);
+              im_hi[2 * j2] = pack_h2(s01.x, s01.y);
+              re_hi[2 * j2 + 1] = pack_h2(c23.x, c23.y);
+              im_hi[2 * j2 + 1] = pack_h2(s23.x, s23.y);
+            }
+          }
+          __syncwarp();
+          const uint32_t hc = acol + 4 * jh;
+          if (NPART == 2) {
+            tmem_st4(hc + 0, re_hi);
+            tmem_st4(hc + 32, re_lo);
+            tmem_st4(hc + 64, im_hi);
+            tmem_st4(hc + 96, im_lo);
+          } else {
+            tmem_st4(hc + 0, re_hi);
+            tmem_st4(hc + 32, im_hi);
+          }
         }
         tmem_st_wait();
         tc_fence_before();
