@@ -36,9 +36,7 @@ constexpr int MMA_WARP = 16;
 constexpr int LOAD_WARP = 17;
 constexpr int NTHREADS = 18 * 32;
 constexpr int NBUF = 2;          // shared-memory stages (one streamed block each)
-constexpr int NSLOT = 2;         // TMEM A slots (one 64-wide half block each)
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t A_COL0 = 256;  // first TMEM column of the A slots
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s
 
 enum Mode { ENC = 0, ADJ = 1 };
@@ -85,10 +83,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n.reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       "selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(20000u)  // suspend hint (ns): sleep, do not spin
       : "memory");
   return ok != 0;
 }
@@ -237,6 +235,14 @@ __host__ __device__ constexpr uint32_t idesc_f16(int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+// Round to 11 significant bits (the FP16 significand), half away from zero, with integer
+// operations on the bit pattern; the result is exactly representable in FP16 for values in
+// the normal FP16 range.
+__device__ __forceinline__ float2 hi11(float2 v) {
+  return make_float2(__uint_as_float((__float_as_uint(v.x) + 0x1000u) & 0xFFFFE000u),
+                     __uint_as_float((__float_as_uint(v.y) + 0x1000u) & 0xFFFFE000u));
+}
+
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
   const __half2 h = __floats2half2_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -250,6 +256,11 @@ struct Smem {
   static constexpr int BROWS = 2 * CP;
   static constexpr int B_HALF_BYTES = NPART * BROWS * 128;  // one 64-wide half
   static constexpr int B_BYTES = 2 * B_HALF_BYTES;           // one streamed block
+  // TMEM: accumulators D1, D2 in columns [0, 4 CP); A slots (one 64-wide half block of
+  // NPART x {re, im} FP16 matrices, 32 columns each) from ACOL0 to the end of the 512.
+  static constexpr uint32_t ACOL0 = 4 * CP > 128 ? 4 * CP : 128;
+  static constexpr int NSLOT_FIT = (int)((512 - ACOL0) / (NPART * 64));
+  static constexpr int NSLOT = NSLOT_FIT > 4 ? 4 : NSLOT_FIT;
 };
 
 template <int MODE, int CP, int RT, int NPART>
@@ -264,13 +275,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   uint8_t* sB = base;                                              // [NBUF][B_BYTES]
   float* sCol = (float*)(sB + NBUF * SM::B_BYTES);                 // [NBUF][RT][128]
   float* sAnc = sCol + NBUF * 128 * RT;                            // [NBUF][128]
-  float2* sRed = (float2*)(sAnc + NBUF * 128);                     // [4][128]
+  float* sRowAnc = sAnc + NBUF * 128;                              // [NBUF][128]
+  float2* sRed = (float2*)(sRowAnc + NBUF * 128);                  // [4][128]
   uint64_t* bars = (uint64_t*)(sRed + 4 * 128);                    // barriers
   uint64_t* full = bars;                      // [NBUF]
   uint64_t* empty = bars + NBUF;              // [NBUF]
-  uint64_t* tfull = bars + 2 * NBUF;          // [NSLOT]
-  uint64_t* tempty = tfull + NSLOT;           // [NSLOT]
-  uint64_t* afull = tempty + NSLOT;           // accumulator full
+  uint64_t* tfull = bars + 2 * NBUF;          // [SM::NSLOT]
+  uint64_t* tempty = tfull + SM::NSLOT;           // [SM::NSLOT]
+  uint64_t* afull = tempty + SM::NSLOT;           // accumulator full
   uint64_t* aempty = afull + 1;               // accumulator drained
   uint64_t* drain = aempty + 1;               // final MMA drain
   uint64_t* ered = drain + 1;                 // ADJ epilogue: partial sums written
@@ -290,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       mbar_init(smem_u32(&full[b]), 1);
       mbar_init(smem_u32(&empty[b]), NGEN_WARPS + 1);
     }
-    for (int s = 0; s < NSLOT; ++s) {
+    for (int s = 0; s < SM::NSLOT; ++s) {
       mbar_init(smem_u32(&tfull[s]), NGEN_WARPS);
       mbar_init(smem_u32(&tempty[s]), 1);
     }
@@ -332,13 +344,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         if (use > 0 && !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1))
           break;
         const uint32_t fb = smem_u32(&full[buf]);
-        mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 512u);
+        mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 1024u);
         bulk_g2s(smem_u32(sB + buf * SM::B_BYTES), p.Bimg + (long long)in * SM::B_BYTES,
                  SM::B_BYTES, fb);
         bulk_g2s(smem_u32(sCol + buf * 128 * RT), p.colT + (long long)in * 128 * RT, col_bytes,
                  fb);
         bulk_g2s(smem_u32(sAnc + buf * 128), p.colAnc + (long long)o * p.cols_total + in * 128,
                  512u, fb);
+        bulk_g2s(smem_u32(sRowAnc + buf * 128),
+                 p.rowAnc + (long long)in * p.rows_total + (long long)o * 128, 512u, fb);
       }
       // wait for the last copies this warp issued (one per buffer) before the CTA can exit
       const long long n = it;
@@ -380,14 +394,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         }
         const uint32_t sbuf = smem_u32(sB + buf * SM::B_BYTES);
         for (int st = 0; st < 2; ++st, ++gstage) {
-          const int slot = (int)(gstage % NSLOT);
-          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / NSLOT) & 1u, abort_flag, p.err,
+          const int slot = (int)(gstage % SM::NSLOT);
+          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / SM::NSLOT) & 1u, abort_flag, p.err,
                          4)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t acol = tmem + A_COL0 + slot * (NPART * 64);
+          const uint32_t acol = tmem + SM::ACOL0 + slot * (NPART * 64);
           const uint32_t bhi = sbuf + st * SM::B_HALF_BYTES;
           const uint32_t blo = bhi + 2 * CP * 128;
 #pragma unroll
@@ -441,8 +455,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
                                          : make_float2(6.283185307179586f, 6.283185307179586f);
     const float2 RND = make_float2(12582912.f, 12582912.f);    // 1.5 * 2^23: round to integer
     const float2 NRND = make_float2(-12582912.f, -12582912.f);
-    const float2 SPL = make_float2(6144.f, 6144.f);            // 1.5 * 2^12: round to 2^-11
-    const float2 NSPL = make_float2(-6144.f, -6144.f);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     float own[RT];
     float2 racc[CW];
@@ -468,25 +480,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 #pragma unroll
         for (int q = 0; q < RT; ++q) own[q] = p.rowT[((long long)o * RT + q) * 128 + row];
       }
-      const float rb = p.rowAnc[(long long)in * p.rows_total + row_g];
-      const float2 rb2 = make_float2(rb, rb);
       if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5)) {
         ok = false;
         break;
       }
       const float* col = sCol + buf * 128 * RT;
       const float* anc = sAnc + buf * 128;
+      const float rb = sRowAnc[buf * 128 + row];
+      const float2 rb2 = make_float2(rb, rb);
       for (int st = 0; st < 2; ++st, ++gstage) {
-        const int slot = (int)(gstage % NSLOT);
-        if (gstage >= NSLOT &&
-            !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / NSLOT - 1) & 1u, abort_flag,
+        const int slot = (int)(gstage % SM::NSLOT);
+        if (gstage >= SM::NSLOT &&
+            !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / SM::NSLOT - 1) & 1u, abort_flag,
                        p.err, 6)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const int c0 = st * 64 + g * 16;
-        const uint32_t acol = tmem + lane_base + A_COL0 + slot * (NPART * 64) + g * 8;
+        const uint32_t acol = tmem + lane_base + SM::ACOL0 + slot * (NPART * 64) + g * 8;
         // two halves of 8 streamed elements (4 TMEM columns per matrix each)
 #pragma unroll
         for (int jh = 0; jh < 2; ++jh) {
@@ -515,11 +527,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
             __sincosf(a23.x, &s23.x, &c23.x);
             __sincosf(a23.y, &s23.y, &c23.y);
             if (NPART == 2) {
-              // hi = value rounded to the 2^-11 grid (exact in FP16 for |v| <= 1), lo = rest
-              const float2 hc01 = __fadd2_rn(__fadd2_rn(c01, SPL), NSPL);
-              const float2 hs01 = __fadd2_rn(__fadd2_rn(s01, SPL), NSPL);
-              const float2 hc23 = __fadd2_rn(__fadd2_rn(c23, SPL), NSPL);
-              const float2 hs23 = __fadd2_rn(__fadd2_rn(s23, SPL), NSPL);
+              // hi = value rounded to 11 significant bits on the integer pipe (exact in
+              // FP16 for |v| <= 1), lo = value - hi on the FMA pipe
+              const float2 hc01 = hi11(c01), hs01 = hi11(s01);
+              const float2 hc23 = hi11(c23), hs23 = hi11(s23);
               re_hi[2 * j2] = pack_h2(hc01.x, hc01.y);
               im_hi[2 * j2] = pack_h2(hs01.x, hs01.y);
               re_hi[2 * j2 + 1] = pack_h2(hc23.x, hc23.y);
@@ -645,8 +656,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
 template <int CP, int RP, int NPART>
 constexpr size_t smem_bytes() {
-  return 1024 + NBUF * Smem<CP, NPART>::B_BYTES + NBUF * 128 * RP * 4 + NBUF * 128 * 4 +
-         4 * 128 * 8 + 16 * 8 + 16;
+  return 1024 + NBUF * Smem<CP, NPART>::B_BYTES + NBUF * 128 * RP * 4 + 2 * NBUF * 128 * 4 +
+         4 * 128 * 8 + 24 * 8 + 16;
 }
 
 // ---------------------------------------------------------------------------------------
