@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     long long cur_o = -1;
     long long row_g = 0;
     for (long long w = w0; w < w1 && ok; ++w, ++it) {
-      const int o = (int)(w / p.n_inner), in = (int)(w % p.n_inner);
+      const int o = (int)(w / p.n_inner);
       const int buf = (int)(it % NBUF);
       const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
       const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
