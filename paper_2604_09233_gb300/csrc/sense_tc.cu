@@ -458,6 +458,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     const float2 NEG1 = make_float2(-1.f, -1.f);
     float own[RT];
     float2 racc[CW];
+    // TMEM stores of a stage complete while the next stage is computed: the stage's
+    // wait::st and "slot full" signal are issued after the first half of the next stage.
+    int pending = -1;
+    auto flush_pending = [&]() {
+      if (pending >= 0) {
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tfull[pending]));
+        pending = -1;
+      }
+    };
     long long it = 0, gstage = 0, run_start = w0;
     int seg = 0, run = 0;
     bool ok = true;
@@ -549,6 +561,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
             }
           }
           __syncwarp();
+          if (jh == 0) flush_pending();
           const uint32_t hc = acol + 4 * jh;
           if (NPART == 2) {
             tmem_st4(hc + 0, re_hi);
@@ -560,10 +573,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
             tmem_st4(hc + 32, im_hi);
           }
         }
-        tmem_st_wait();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&tfull[slot]));
+        pending = slot;
       }
       if (!ok) break;
       __syncwarp();
@@ -571,6 +581,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
       if (seg_last) {
         // ------------------------------------------------ segment drain into registers
+        flush_pending();
         if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7)) {
           ok = false;
           break;
@@ -641,6 +652,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         ++run;
       }
     }
+    if (ok) flush_pending();
     (void)ok;
   }
 
