@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   using SM = Smem<CP, NPART>;
   constexpr int CW = CP / 4;  // coils per warpgroup in the epilogue
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-align the dynamic shared memory base
-  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // 1024-align the dynamic shared memory base by pointer arithmetic on the __shared__
+  // array itself, so the compiler keeps the shared address space (shared-memory loads,
+  // not generic ones)
+  uint8_t* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sB = base;                                              // [NBUF][B_BYTES]
   float* sCol = (float*)(sB + NBUF * SM::B_BYTES);                 // [NBUF][RT][128]
   float* sAnc = sCol + NBUF * 128 * RT;                            // [NBUF][128]
