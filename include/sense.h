@@ -143,6 +143,22 @@ int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opt
  * wins. Host-only. *corner = -1 when n < 3. Errors: EINVAL. */
 int sense_lcurve_corner(const double* history, int32_t n, int32_t* corner);
 
+/* Tuning ------------------------------------------------------------------------------
+ * (no counterpart in the paper: execution parameters of the tensor-core kernels)
+ *   seg_len  the tensor-core passes accumulate at most this many 128 x 128 (sample, voxel)
+ *            blocks in one FP32 tensor-memory accumulator before adding it to a running
+ *            sum; shorter = more accurate, longer = fewer drains. 1..64, default 8.
+ *   grid     persistent CTAs of a tensor-core pass; 0 = one per SM (default). */
+typedef struct {
+  int32_t seg_len;
+  int32_t grid;
+  int32_t reserved[6];
+} sense_tuning;
+
+int sense_plan_get_tuning(sense_plan plan, sense_tuning* out);
+/* Errors: EINVAL (out-of-range value; the plan is left unchanged), ENOMEM, ECUDA. */
+int sense_plan_set_tuning(sense_plan plan, const sense_tuning* t);
+
 /* Diagnostics -------------------------------------------------------------------------
  * (no counterpart in the paper: measurement support for the kernels above)
  * Kernel classes: 0 = tensor-core E pass, 1 = tensor-core E^H pass, 2 = FP32 E kernel,

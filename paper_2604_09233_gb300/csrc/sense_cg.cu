@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(VB) cg_update_kernel(float2* x, float2* r,
   double tot[4];
   if (finish_sums<4>(v, part, counter, tot)) {
     const double rr_old = scal[SC_RR];
+    scal[SC_RR_PREV] = rr_old;
     const double rr = tot[0];
     const int it = (int)scal[SC_ITER] + 1;
     scal[SC_ITER] = (double)it;
@@ -249,6 +250,48 @@ __global__ void __launch_bounds__(VB) cg_update_kernel(float2* x, float2* r,
     }
     scal[SC_RR] = rr;
     scal[SC_B_RE] = rr / rr_old;   // steps 13-15: alpha_new / beta with beta = alpha_old
+    scal[SC_B_IM] = 0.0;
+    if (scal[SC_TOL2] > 0.0 && rr <= scal[SC_TOL2]) scal[SC_STOP] = 1.0;
+  }
+}
+
+// Residual replacement (van der Vorst and Ye): after the update of an iteration, the
+// recursively updated residual is replaced by the true one, r = b - E^H E x, computed
+// with the FP32 operator into q; the step-15 ratio and the history row are recomputed
+// from it.
+__global__ void __launch_bounds__(VB) cg_replace_kernel(const float2* __restrict__ x, float2* r,
+                                                        const float2* __restrict__ b,
+                                                        const float2* __restrict__ q,
+                                                        int64_t Lp, double* part,
+                                                        unsigned* counter, double* scal,
+                                                        double* hist) {
+  if (stopped(scal)) return;
+  __shared__ double sh[3 * VB / 32];
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Lp;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 bi = b[i], qi = q[i], xi = x[i];
+    const float2 ri = make_float2(bi.x - qi.x, bi.y - qi.y);
+    r[i] = ri;
+    v[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    v[1] += (double)xi.x * bi.x + (double)xi.y * bi.y;
+    v[2] += (double)xi.x * ri.x + (double)xi.y * ri.y;
+  }
+  block_sum<3>(v, sh);
+  double tot[3];
+  if (finish_sums<3>(v, part, counter, tot)) {
+    const int it = (int)scal[SC_ITER];
+    const double rr = tot[0];
+    if (hist) {
+      hist[3 * it + 0] = sqrt(rr);
+      hist[3 * it + 2] = sqrt(fmax(0.0, scal[SC_SS] - tot[1] - tot[2]));
+    }
+    if (!isfinite(rr)) {
+      scal[SC_STOP] = 3.0;
+      return;
+    }
+    scal[SC_RR] = rr;
+    scal[SC_B_RE] = rr / scal[SC_RR_PREV];
     scal[SC_B_IM] = 0.0;
     if (scal[SC_TOL2] > 0.0 && rr <= scal[SC_TOL2]) scal[SC_STOP] = 1.0;
   }
@@ -473,7 +516,10 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   count_launch(P);
   // step 3: b = E^H sigma (FP32 operator, or the split tensor-core operator when the
   // iterations use it)
-  const int prec_b = opts->prec == SENSE_PREC_TC_SPLIT ? SENSE_PREC_TC_SPLIT : SENSE_PREC_FP32;
+  // (FP32 whenever the residual is refined: b enters every replaced residual)
+  const int prec_b = (opts->prec == SENSE_PREC_TC_SPLIT && opts->refine_every == 0)
+                         ? SENSE_PREC_TC_SPLIT
+                         : SENSE_PREC_FP32;
   TRY(adjoint_internal(P, prec_b, P->Ydata, P->vb, nullptr, st));
   cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
                                     P->scal, P->hist, opts->rel_tol, N);
@@ -489,7 +535,16 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
     cg_update_kernel<<<vb, VB, 0, st>>>(P->vx, P->vr, P->vp, P->vq, P->vb, P->Lp, P->red,
                                         P->counter, P->scal, P->hist);
     SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
+    count_launch(P);
+    if (opts->prec != SENSE_PREC_FP32 && opts->refine_every > 0 &&
+        (n + 1) % opts->refine_every == 0 && n + 1 < N) {
+      // residual replacement with the FP32 operator
+      TRY(apply_normal_internal(P, SENSE_PREC_FP32, P->vx, P->vm, stop, st));
+      cg_replace_kernel<<<vb, VB, 0, st>>>(P->vx, P->vr, P->vb, P->vm, P->Lp, P->red,
+                                           P->counter, P->scal, P->hist);
+      SENSE_CUDA_TRY(cudaGetLastError());
+      count_launch(P);
+    }
     cg_p_kernel<<<vb, VB, 0, st>>>(P->vp, P->vr, P->Lp, P->scal);
     SENSE_CUDA_TRY(cudaGetLastError());
   count_launch(P);

@@ -61,6 +61,19 @@ __global__ void sincos_probe_kernel(int iters, float* sink) {
 
 using namespace sense;
 
+extern "C" int sense_plan_get_tuning(sense_plan P, sense_tuning* out) {
+  if (!P || !out) return set_error(SENSE_EINVAL, "null plan or output");
+  *out = sense_tuning{};
+  out->seg_len = P->tc_seg_len;
+  out->grid = P->tc_grid == P->num_sms ? 0 : P->tc_grid;
+  return SENSE_OK;
+}
+
+extern "C" int sense_plan_set_tuning(sense_plan P, const sense_tuning* t) {
+  if (!P || !t) return set_error(SENSE_EINVAL, "null plan or tuning");
+  return tc_set_tuning(P, t->seg_len, t->grid);
+}
+
 extern "C" int sense_plan_profile(sense_plan P, int enable) {
   if (!P) return set_error(SENSE_EINVAL, "null plan");
   P->prof_on = enable != 0;

@@ -33,6 +33,7 @@ enum ScalarSlot {
   SC_ITER,         // iterations completed
   SC_TOL2,         // rel_tol^2 * rr0 (0 disables)
   SC_MAXIT,        // N_It
+  SC_RR_PREV,      // r^H r of the previous iteration (for a replaced residual)
   SC_COUNT
 };
 
@@ -164,6 +165,7 @@ int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, fl
 int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool colmax_ready,
                const double* stop, cudaStream_t st);
 int tc_check_error(sense_plan_s* P);
+int tc_set_tuning(sense_plan_s* P, int seg_len, int grid);
 
 // diagnostics (sense_diag.cu) ----------------------------------------------------------
 enum KernelClass { KC_TC_ENC = 0, KC_TC_ADJ = 1, KC_F32_ENC = 2, KC_F32_ADJ = 3 };

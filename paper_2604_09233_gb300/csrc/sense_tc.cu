@@ -821,8 +821,17 @@ static int dispatch_cp(sense_plan_s* P, const tc::Params& prm, int G, cudaStream
   }
 }
 
-int tc_setup(sense_plan_s* P) {
-  P->tc_grid = P->num_sms;
+static void tc_free_layout(sense_plan_s* P) {
+  cudaFree(P->tc_first_e); cudaFree(P->tc_nslot_e); cudaFree(P->tc_first_a);
+  cudaFree(P->tc_nslot_a); cudaFree(P->Ypart_tc); cudaFree(P->Xpart_tc);
+  P->tc_first_e = P->tc_nslot_e = P->tc_first_a = P->tc_nslot_a = nullptr;
+  P->Ypart_tc = P->Xpart_tc = nullptr;
+}
+
+// Stream-K layout for the current grid: per row block, its first contributing CTA and its
+// number of partial slots; partial buffers sized for the largest slot count.
+static int tc_layout(sense_plan_s* P) {
+  tc_free_layout(P);
   std::vector<int> fe, ne, fa, na;
   stream_k_layout(P->nsb, P->nvb, P->tc_grid, fe, ne, &P->tc_slots_e);
   stream_k_layout(P->nvb, P->nsb, P->tc_grid, fa, na, &P->tc_slots_a);
@@ -839,6 +848,18 @@ int tc_setup(sense_plan_s* P) {
   if ((rc = up(&P->tc_nslot_e, ne)) != SENSE_OK) return rc;
   if ((rc = up(&P->tc_first_a, fa)) != SENSE_OK) return rc;
   if ((rc = up(&P->tc_nslot_a, na)) != SENSE_OK) return rc;
+  if (cudaMalloc((void**)&P->Ypart_tc, (size_t)P->tc_slots_e * P->Kp * P->Cp * 8) != cudaSuccess ||
+      cudaMalloc((void**)&P->Xpart_tc, (size_t)P->tc_slots_a * P->Lp * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SENSE_ENOMEM, "tc partial buffers");
+  }
+  return SENSE_OK;
+}
+
+int tc_setup(sense_plan_s* P) {
+  P->tc_grid = P->num_sms;
+  int rc;
+  if ((rc = tc_layout(P)) != SENSE_OK) return rc;
   const size_t img_q = (size_t)P->nvb * 2 * 2 * (2 * P->Cp) * 128;   // sized for NPART = 2
   const size_t img_y = (size_t)P->nsb * 2 * 2 * (2 * P->Cp) * 128;
   auto al = [&](void** d, size_t bytes) -> int {
@@ -853,19 +874,28 @@ int tc_setup(sense_plan_s* P) {
   if ((rc = al((void**)&P->qscale, P->Cp * 4)) != SENSE_OK) return rc;
   if ((rc = al((void**)&P->yscale, P->Cp * 4)) != SENSE_OK) return rc;
   if ((rc = al((void**)&P->colmax, 2 * P->Cp * 4)) != SENSE_OK) return rc;
-  if ((rc = al((void**)&P->Ypart_tc, (size_t)P->tc_slots_e * P->Kp * P->Cp * 8)) != SENSE_OK)
-    return rc;
-  if ((rc = al((void**)&P->Xpart_tc, (size_t)P->tc_slots_a * P->Lp * 8)) != SENSE_OK) return rc;
   if ((rc = al((void**)&P->tc_err, 4)) != SENSE_OK) return rc;
   SENSE_CUDA_TRY(cudaMemset(P->tc_err, 0, 4));
   return SENSE_OK;
 }
 
 void tc_free(sense_plan_s* P) {
-  cudaFree(P->tc_first_e); cudaFree(P->tc_nslot_e); cudaFree(P->tc_first_a);
-  cudaFree(P->tc_nslot_a); cudaFree(P->Qimg); cudaFree(P->Yimg); cudaFree(P->qscale);
-  cudaFree(P->yscale); cudaFree(P->colmax); cudaFree(P->Ypart_tc); cudaFree(P->Xpart_tc);
-  cudaFree(P->tc_err);
+  tc_free_layout(P);
+  cudaFree(P->Qimg); cudaFree(P->Yimg); cudaFree(P->qscale);
+  cudaFree(P->yscale); cudaFree(P->colmax); cudaFree(P->tc_err);
+}
+
+int tc_set_tuning(sense_plan_s* P, int seg_len, int grid) {
+  if (seg_len < 1 || seg_len > 64 || grid < 0 || grid > 64 * P->num_sms)
+    return set_error(SENSE_EINVAL, "seg_len must be 1..64 and grid 0..64 x SMs");
+  const int g = grid == 0 ? P->num_sms : grid;
+  P->tc_seg_len = seg_len;
+  if (g != P->tc_grid) {
+    SENSE_CUDA_TRY(cudaDeviceSynchronize());
+    P->tc_grid = g;
+    return tc_layout(P);
+  }
+  return SENSE_OK;
 }
 
 // Y_int[k][c] = sum over the stream-K slots of sample block k/128 (0 for padding);

@@ -27,7 +27,8 @@ PRECISIONS = {"fp32": SENSE_PREC_FP32, "tc_fp16": SENSE_PREC_TC_FP16,
 EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sense_plan_info",
             "sense_encode", "sense_adjoint", "sense_normal_op", "sense_cg_solve",
             "sense_lcurve_corner", "sense_strerror", "sense_last_error", "sense_plan_profile",
-            "sense_plan_stats", "sense_diag_sincos_rate"]
+            "sense_plan_stats", "sense_diag_sincos_rate", "sense_plan_get_tuning",
+            "sense_plan_set_tuning"]
 
 
 class SenseError(RuntimeError):
@@ -44,6 +45,11 @@ class Stats(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["tc_encode_pass", "tc_adjoint_pass", "fp32_encode", "fp32_adjoint"]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("seg_len", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class _Problem(ctypes.Structure):
@@ -80,6 +86,8 @@ def _load():
                            ctypes.c_int),
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
+        "sense_plan_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "sense_plan_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
         "sense_diag_sincos_rate": ([dbl, ctypes.POINTER(dbl)], ctypes.c_int),
         "sense_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -201,6 +209,17 @@ def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refi
                                _stream(ss, sx, explicit=stream)), "sense_cg_solve")
     out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
     return out, (None if hist is None else hist[: info.iters + 1])
+
+
+def sense_plan_get_tuning(plan):
+    t = Tuning()
+    _check(_lib.sense_plan_get_tuning(plan, ctypes.byref(t)), "sense_plan_get_tuning")
+    return {"seg_len": t.seg_len, "grid": t.grid}
+
+
+def sense_plan_set_tuning(plan, seg_len=8, grid=0):
+    t = Tuning(int(seg_len), int(grid))
+    _check(_lib.sense_plan_set_tuning(plan, ctypes.byref(t)), "sense_plan_set_tuning")
 
 
 def sense_plan_profile(plan, enable=True):
