@@ -105,7 +105,7 @@ struct sense_plan_s {
 
   // tensor-core path (sense_tc.cu)
   int tc_grid = 0;                 // persistent CTAs (one per SM)
-  int tc_seg_len = 8;              // drain the TMEM accumulators every this many pairs
+  int tc_seg_len = 4;              // drain the TMEM accumulators every this many pairs
   int tc_slots_e = 1, tc_slots_a = 1;
   int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E
   int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [nvb] stream-K slots of E^H

@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   float* sAnc = sCol + NBUF * 128 * RT;                            // [NBUF][128]
   float* sRowAnc = sAnc + NBUF * 128;                              // [NBUF][128]
   float2* sRed = (float2*)(sRowAnc + NBUF * 128);                  // [4][128]
-  uint64_t* bars = (uint64_t*)(sRed + 4 * 128);                    // barriers
+  float2* sRacc = sRed + 4 * 128;                                  // [CP/4][512]
+  uint64_t* bars = (uint64_t*)(sRacc + (CP / 4) * NGEN_WARPS * 32); // barriers
   uint64_t* full = bars;                      // [NBUF]
   uint64_t* empty = bars + NBUF;              // [NBUF]
   uint64_t* tfull = bars + 2 * NBUF;          // [SM::NSLOT]
@@ -459,7 +460,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     const float2 NRND = make_float2(-12582912.f, -12582912.f);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     float own[RT];
-    float2 racc[CW];
+    // per-thread running sum of the run, in shared memory (frees registers for the
+    // generator): element c of this thread at racc[c * NGEN_THREADS]
+    float2* racc = sRacc + threadIdx.x;
+    constexpr int NGT = NGEN_WARPS * 32;
     // TMEM stores of a stage complete while the next stage is computed: the stage's
     // wait::st and "slot full" signal are issued after the first half of the next stage.
     int pending = -1;
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       if (first_in_run) {
         run_start = w;
 #pragma unroll
-        for (int c = 0; c < CW; ++c) racc[c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
       }
       const bool seg_last = last_in_run || ((w - run_start + 1) % F == 0);
       if (o != cur_o) {
@@ -517,49 +521,49 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 #pragma unroll
         for (int jh = 0; jh < 2; ++jh) {
           uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
-#pragma unroll
-          for (int j2 = 0; j2 < 2; ++j2) {
-            const int v0 = c0 + 8 * jh + 4 * j2;
+          {
+            // 8 streamed elements as 4 independent two-element chains
+            const int v0 = c0 + 8 * jh;
             const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
+            const float4 a8 = *reinterpret_cast<const float4*>(anc + v0 + 4);
             // theta (turns) = A + B + sum_q own_q * delta_q, two pairs per instruction
-            float2 t01 = __fadd2_rn(make_float2(a4.x, a4.y), rb2);
-            float2 t23 = __fadd2_rn(make_float2(a4.z, a4.w), rb2);
+            float2 t[4];
+            t[0] = __fadd2_rn(make_float2(a4.x, a4.y), rb2);
+            t[1] = __fadd2_rn(make_float2(a4.z, a4.w), rb2);
+            t[2] = __fadd2_rn(make_float2(a8.x, a8.y), rb2);
+            t[3] = __fadd2_rn(make_float2(a8.z, a8.w), rb2);
 #pragma unroll
             for (int q = 0; q < RT; ++q) {
               const float4 d = *reinterpret_cast<const float4*>(col + q * 128 + v0);
+              const float4 e = *reinterpret_cast<const float4*>(col + q * 128 + v0 + 4);
               const float2 o2 = make_float2(own[q], own[q]);
-              t01 = __ffma2_rn(o2, make_float2(d.x, d.y), t01);
-              t23 = __ffma2_rn(o2, make_float2(d.z, d.w), t23);
+              t[0] = __ffma2_rn(o2, make_float2(d.x, d.y), t[0]);
+              t[1] = __ffma2_rn(o2, make_float2(d.z, d.w), t[1]);
+              t[2] = __ffma2_rn(o2, make_float2(e.x, e.y), t[2]);
+              t[3] = __ffma2_rn(o2, make_float2(e.z, e.w), t[3]);
             }
-            // reduce to [-1/2, 1/2] turn: t - rint(t)
-            t01 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t01, RND), NRND), NEG1, t01);
-            t23 = __ffma2_rn(__fadd2_rn(__fadd2_rn(t23, RND), NRND), NEG1, t23);
-            const float2 a01 = __fmul2_rn(t01, ang_scale), a23 = __fmul2_rn(t23, ang_scale);
-            float2 c01, s01, c23, s23;
-            __sincosf(a01.x, &s01.x, &c01.x);
-            __sincosf(a01.y, &s01.y, &c01.y);
-            __sincosf(a23.x, &s23.x, &c23.x);
-            __sincosf(a23.y, &s23.y, &c23.y);
-            if (NPART == 2) {
-              // hi = value rounded to 11 significant bits on the integer pipe (exact in
-              // FP16 for |v| <= 1), lo = value - hi on the FMA pipe
-              const float2 hc01 = hi11(c01), hs01 = hi11(s01);
-              const float2 hc23 = hi11(c23), hs23 = hi11(s23);
-              re_hi[2 * j2] = pack_h2(hc01.x, hc01.y);
-              im_hi[2 * j2] = pack_h2(hs01.x, hs01.y);
-              re_hi[2 * j2 + 1] = pack_h2(hc23.x, hc23.y);
-              im_hi[2 * j2 + 1] = pack_h2(hs23.x, hs23.y);
-              const float2 lc01 = __ffma2_rn(hc01, NEG1, c01), ls01 = __ffma2_rn(hs01, NEG1, s01);
-              const float2 lc23 = __ffma2_rn(hc23, NEG1, c23), ls23 = __ffma2_rn(hs23, NEG1, s23);
-              re_lo[2 * j2] = pack_h2(lc01.x, lc01.y);
-              im_lo[2 * j2] = pack_h2(ls01.x, ls01.y);
-              re_lo[2 * j2 + 1] = pack_h2(lc23.x, lc23.y);
-              im_lo[2 * j2 + 1] = pack_h2(ls23.x, ls23.y);
-            } else {
-              re_hi[2 * j2] = pack_h2(c01.x, c01.y);
-              im_hi[2 * j2] = pack_h2(s01.x, s01.y);
-              re_hi[2 * j2 + 1] = pack_h2(c23.x, c23.y);
-              im_hi[2 * j2 + 1] = pack_h2(s23.x, s23.y);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              // reduce to [-1/2, 1/2] turn: t - rint(t); then radians (sign: conjugate
+              // tile for the E^H pass)
+              const float2 tr = __ffma2_rn(__fadd2_rn(__fadd2_rn(t[k], RND), NRND), NEG1, t[k]);
+              const float2 ang = __fmul2_rn(tr, ang_scale);
+              float2 cs, sn;
+              __sincosf(ang.x, &sn.x, &cs.x);
+              __sincosf(ang.y, &sn.y, &cs.y);
+              if (NPART == 2) {
+                // hi = value rounded to 11 significant bits on the integer pipe (exact in
+                // FP16 for |v| <= 1), lo = value - hi on the FMA pipe
+                const float2 hc = hi11(cs), hs = hi11(sn);
+                re_hi[k] = pack_h2(hc.x, hc.y);
+                im_hi[k] = pack_h2(hs.x, hs.y);
+                const float2 lc = __ffma2_rn(hc, NEG1, cs), ls = __ffma2_rn(hs, NEG1, sn);
+                re_lo[k] = pack_h2(lc.x, lc.y);
+                im_lo[k] = pack_h2(ls.x, ls.y);
+              } else {
+                re_hi[k] = pack_h2(cs.x, cs.y);
+                im_hi[k] = pack_h2(sn.x, sn.y);
+              }
             }
           }
           __syncwarp();
@@ -600,8 +604,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         if (lane == 0) mbar_arrive(smem_u32(aempty));
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-          racc[c].x += d1r[c] - d2i[c];
-          racc[c].y += d1i[c] + d2r[c];
+          float2 a = racc[c * NGT];
+          a.x += d1r[c] - d2i[c];
+          a.y += d1i[c] + d2r[c];
+          racc[c * NGT] = a;
         }
         ++seg;
       }
@@ -613,7 +619,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 #pragma unroll
           for (int c = 0; c < CW; ++c) {
             const float sc = p.bscale[cbase + c];
-            dst[c] = make_float2(racc[c].x * sc, racc[c].y * sc);
+            const float2 a = racc[c * NGT];
+            dst[c] = make_float2(a.x * sc, a.y * sc);
           }
         } else {
           const float2* Srow = p.S + row_g * CP + cbase;
@@ -621,7 +628,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 #pragma unroll
           for (int c = 0; c < CW; ++c) {
             const float sc = p.bscale[cbase + c];
-            const float xr = racc[c].x * sc, xi = racc[c].y * sc;
+            const float2 a = racc[c * NGT];
+            const float xr = a.x * sc, xi = a.y * sc;
             const float2 s = Srow[c];
             acc.x = fmaf(s.x, xr, fmaf(s.y, xi, acc.x));
             acc.y = fmaf(s.x, xi, fmaf(-s.y, xr, acc.y));
@@ -671,7 +679,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 template <int CP, int RP, int NPART>
 constexpr size_t smem_bytes() {
   return 1024 + NBUF * Smem<CP, NPART>::B_BYTES + NBUF * 128 * RP * 4 + 2 * NBUF * 128 * 4 +
-         4 * 128 * 8 + 24 * 8 + 16;
+         4 * 128 * 8 + (CP / 4) * NGEN_WARPS * 32 * 8 + 24 * 8 + 16;
 }
 
 // ---------------------------------------------------------------------------------------
