@@ -35,7 +35,6 @@ constexpr int NGEN_WARPS = 16;
 constexpr int MMA_WARP = 16;
 constexpr int LOAD_WARP = 17;
 constexpr int NTHREADS = 18 * 32;
-constexpr int NBUF = 2;          // shared-memory stages (one streamed block each)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s
 
@@ -261,6 +260,8 @@ struct Smem {
   static constexpr uint32_t ACOL0 = 4 * CP > 128 ? 4 * CP : 128;
   static constexpr int NSLOT_FIT = (int)((512 - ACOL0) / (NPART * 64));
   static constexpr int NSLOT = NSLOT_FIT > 4 ? 4 : NSLOT_FIT;
+  // shared-memory stages of streamed blocks (three fit below 64 coils)
+  static constexpr int NBUFS = CP <= 32 ? 3 : 2;
 };
 
 template <int MODE, int CP, int RT, int NPART>
@@ -268,6 +269,7 @@ template <int MODE, int CP, int RT, int NPART>
 // 96 registers per thread is the ceiling; one CTA per SM.
 __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   using SM = Smem<CP, NPART>;
+  constexpr int NBUF = SM::NBUFS;
   constexpr int CW = CP / 4;  // coils per warpgroup in the epilogue
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-align the dynamic shared memory base by pointer arithmetic on the __shared__
@@ -481,16 +483,89 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     bool ok = true;
     long long cur_o = -1;
     long long row_g = 0;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
+    // A segment's accumulators are drained after the next stage has been generated, so
+    // the generators never wait for the tensor core at segment ends.
+    bool drain_due = false, d_out = false;
+    long long d_o = 0, d_row = 0;
+    // Add the segment accumulators to the running sums; at the end of a run also write
+    // the run's output and clear the running sums.
+    auto drain = [&]() -> bool {
+      drain_due = false;
+      if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7)) return false;
+      tc_fence_after();
+      float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
+      const uint32_t lb = tmem + lane_base;
+      tmem_ld<CW>(lb + cbase, d1r);               // D1[:, c]      = A_re B_re
+      tmem_ld<CW>(lb + CP + cbase, d1i);          // D1[:, C+c]    = A_re B_im
+      tmem_ld<CW>(lb + 2 * CP + cbase, d2r);      // D2[:, c]      = A_im B_re
+      tmem_ld<CW>(lb + 3 * CP + cbase, d2i);      // D2[:, C+c]    = A_im B_im
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(aempty));
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        float2 a = racc[c * NGT];
+        a.x += d1r[c] - d2i[c];
+        a.y += d1i[c] + d2r[c];
+        racc[c * NGT] = a;
+      }
+      ++seg;
+      if (!d_out) return true;
+      // ---------------------------------------------------------------- run output
+      const long long slot_o = i - p.first_cta[d_o];
+      if (MODE == ENC) {
+        float2* dst = p.out + (slot_o * p.rows_total + d_row) * CP + cbase;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const float sc = p.bscale[cbase + c];
+          const float2 a = racc[c * NGT];
+          dst[c] = make_float2(a.x * sc, a.y * sc);
+        }
+      } else {
+        const float2* Srow = p.S + d_row * CP + cbase;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const float sc = p.bscale[cbase + c];
+          const float2 a = racc[c * NGT];
+          const float xr = a.x * sc, xi = a.y * sc;
+          const float2 sv = Srow[c];
+          acc.x = fmaf(sv.x, xr, fmaf(sv.y, xi, acc.x));
+          acc.y = fmaf(sv.x, xi, fmaf(-sv.y, xr, acc.y));
+        }
+        // combine the four warpgroups' coil ranges through shared memory (bounded
+        // mbarrier waits, no unbounded named barrier)
+        if (run > 0 &&
+            !warp_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8))
+          return false;
+        sRed[g * 128 + row] = acc;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(ered));
+        if (g == 0) {
+          if (!warp_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8)) return false;
+          float2 v = sRed[row];
+          for (int k = 1; k < 4; ++k) {
+            v.x += sRed[k * 128 + row].x;
+            v.y += sRed[k * 128 + row].y;
+          }
+          p.out[slot_o * p.rows_total + d_row] = v;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(edone));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
+      ++run;
+      return true;
+    };
     for (long long w = w0; w < w1 && ok; ++w, ++it) {
       const int o = (int)(w / p.n_inner);
       const int buf = (int)(it % NBUF);
       const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
       const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
-      if (first_in_run) {
-        run_start = w;
-#pragma unroll
-        for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
-      }
+      if (first_in_run) run_start = w;
       const bool seg_last = last_in_run || ((w - run_start + 1) % F == 0);
       if (o != cur_o) {
         cur_o = o;
@@ -580,87 +655,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           }
         }
         pending = slot;
+        if (st == 0 && drain_due && !drain()) {
+          ok = false;
+          break;
+        }
       }
       if (!ok) break;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[buf]));
-
       if (seg_last) {
-        // ------------------------------------------------ segment drain into registers
-        flush_pending();
-        if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
-        const uint32_t lb = tmem + lane_base;
-        tmem_ld<CW>(lb + cbase, d1r);               // D1[:, c]      = A_re B_re
-        tmem_ld<CW>(lb + CP + cbase, d1i);          // D1[:, C+c]    = A_re B_im
-        tmem_ld<CW>(lb + 2 * CP + cbase, d2r);      // D2[:, c]      = A_im B_re
-        tmem_ld<CW>(lb + 3 * CP + cbase, d2i);      // D2[:, C+c]    = A_im B_im
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(aempty));
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-          float2 a = racc[c * NGT];
-          a.x += d1r[c] - d2i[c];
-          a.y += d1i[c] + d2r[c];
-          racc[c * NGT] = a;
-        }
-        ++seg;
+        // drain after the next stage has been generated (or at the end)
+        drain_due = true;
+        d_out = last_in_run;
+        d_o = o;
+        d_row = row_g;
       }
-      if (last_in_run) {
-        // ------------------------------------------------ run output
-        const long long slot_o = i - p.first_cta[o];
-        if (MODE == ENC) {
-          float2* dst = p.out + (slot_o * p.rows_total + row_g) * CP + cbase;
-#pragma unroll
-          for (int c = 0; c < CW; ++c) {
-            const float sc = p.bscale[cbase + c];
-            const float2 a = racc[c * NGT];
-            dst[c] = make_float2(a.x * sc, a.y * sc);
-          }
-        } else {
-          const float2* Srow = p.S + row_g * CP + cbase;
-          float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int c = 0; c < CW; ++c) {
-            const float sc = p.bscale[cbase + c];
-            const float2 a = racc[c * NGT];
-            const float xr = a.x * sc, xi = a.y * sc;
-            const float2 s = Srow[c];
-            acc.x = fmaf(s.x, xr, fmaf(s.y, xi, acc.x));
-            acc.y = fmaf(s.x, xi, fmaf(-s.y, xr, acc.y));
-          }
-          // combine the four warpgroups' coil ranges through shared memory (bounded
-          // mbarrier waits, no unbounded named barrier)
-          if (run > 0 &&
-              !warp_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8)) {
-            ok = false;
-            break;
-          }
-          sRed[g * 128 + row] = acc;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(ered));
-          if (g == 0) {
-            if (!warp_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8)) {
-              ok = false;
-              break;
-            }
-            float2 v = sRed[row];
-            for (int k = 1; k < 4; ++k) {
-              v.x += sRed[k * 128 + row].x;
-              v.y += sRed[k * 128 + row].y;
-            }
-            p.out[slot_o * p.rows_total + row_g] = v;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(edone));
-          }
-        }
-        ++run;
-      }
+    }
+    if (ok && drain_due) {
+      flush_pending();
+      ok = drain();
     }
     if (ok) flush_pending();
     (void)ok;
@@ -678,7 +691,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
 template <int CP, int RP, int NPART>
 constexpr size_t smem_bytes() {
-  return 1024 + NBUF * Smem<CP, NPART>::B_BYTES + NBUF * 128 * RP * 4 + 2 * NBUF * 128 * 4 +
+  constexpr int NB = Smem<CP, NPART>::NBUFS;
+  return 1024 + NB * Smem<CP, NPART>::B_BYTES + NB * 128 * RP * 4 + 2 * NB * 128 * 4 +
          4 * 128 * 8 + (CP / 4) * NGEN_WARPS * 32 * 8 + 24 * 8 + 16;
 }
 
