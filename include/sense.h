@@ -92,6 +92,12 @@ int sense_plan_destroy(sense_plan plan);
  * ENONFINITE, ECUDA. Stream-ordered on `stream`. */
 int sense_plan_set_b0(sense_plan plan, const double* omega, void* stream);
 
+/* Wait for the plan's work on `stream` and report a device-side failure recorded since the
+ * last check (SENSE_ETIMEOUT when a tensor-core kernel gave up waiting; its outputs are
+ * then invalid). Device-pointer calls are asynchronous and report such failures only here
+ * or in a later synchronising call. Errors: EINVAL, ECUDA, ETIMEOUT. */
+int sense_plan_sync(sense_plan plan, void* stream);
+
 /* Plan dimensions: out[0]=L, out[1]=K, out[2]=C, out[3]=P1, out[4]=number of basis rows
  * kept in the FP32 bilinear part, out[5]=padded L, out[6]=padded K, out[7]=padded C. */
 int sense_plan_info(sense_plan plan, int64_t out[8]);

@@ -61,6 +61,12 @@ __global__ void sincos_probe_kernel(int iters, float* sink) {
 
 using namespace sense;
 
+extern "C" int sense_plan_sync(sense_plan P, void* stream) {
+  if (!P) return set_error(SENSE_EINVAL, "null plan");
+  SENSE_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return tc_check_error(P);
+}
+
 extern "C" int sense_plan_get_tuning(sense_plan P, sense_tuning* out) {
   if (!P || !out) return set_error(SENSE_EINVAL, "null plan or output");
   *out = sense_tuning{};

@@ -28,7 +28,7 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_encode", "sense_adjoint", "sense_normal_op", "sense_cg_solve",
             "sense_lcurve_corner", "sense_strerror", "sense_last_error", "sense_plan_profile",
             "sense_plan_stats", "sense_diag_sincos_rate", "sense_plan_get_tuning",
-            "sense_plan_set_tuning"]
+            "sense_plan_set_tuning", "sense_plan_sync"]
 
 
 class SenseError(RuntimeError):
@@ -86,6 +86,7 @@ def _load():
                            ctypes.c_int),
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
+        "sense_plan_sync": ([vp, vp], ctypes.c_int),
         "sense_plan_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
@@ -211,6 +212,18 @@ def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refi
     return out, (None if hist is None else hist[: info.iters + 1])
 
 
+def sense_plan_sync(plan, stream=None):
+    """Synchronise and raise SenseError if a device-side failure was recorded."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+    _check(_lib.sense_plan_sync(plan, stream), "sense_plan_sync")
+
+
 def sense_plan_get_tuning(plan):
     t = Tuning()
     _check(_lib.sense_plan_get_tuning(plan, ctypes.byref(t)), "sense_plan_get_tuning")
@@ -289,18 +302,21 @@ class Plan:
         import torch
         s = torch.empty((self.K, self.C), dtype=torch.complex64, device=m.device)
         sense_encode(self.handle, prec, m, s)
+        sense_plan_sync(self.handle)
         return s
 
     def adjoint(self, s, prec=SENSE_PREC_FP32):
         import torch
         m = torch.empty((self.L,), dtype=torch.complex64, device=s.device)
         sense_adjoint(self.handle, prec, s, m)
+        sense_plan_sync(self.handle)
         return m
 
     def normal(self, m, prec=SENSE_PREC_FP32):
         import torch
         out = torch.empty((self.L,), dtype=torch.complex64, device=m.device)
         sense_normal_op(self.handle, prec, m, out)
+        sense_plan_sync(self.handle)
         return out
 
     def cg(self, s, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refine_every=0, apply_j=True):
@@ -308,4 +324,5 @@ class Plan:
         x = torch.empty((self.L,), dtype=torch.complex64, device=s.device)
         info, hist = sense_cg_solve(self.handle, s, x, max_iter, prec, rel_tol, refine_every,
                                     apply_j)
+        sense_plan_sync(self.handle)
         return x, info, hist
