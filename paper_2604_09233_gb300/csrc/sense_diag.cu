@@ -71,7 +71,7 @@ extern "C" int sense_plan_get_tuning(sense_plan P, sense_tuning* out) {
   if (!P || !out) return set_error(SENSE_EINVAL, "null plan or output");
   *out = sense_tuning{};
   out->seg_len = P->tc_seg_len;
-  out->grid = P->tc_grid == P->num_sms ? 0 : P->tc_grid;
+  out->grid = P->tc_grid_req == P->num_sms ? 0 : P->tc_grid_req;
   return SENSE_OK;
 }
 

@@ -104,7 +104,8 @@ struct sense_plan_s {
   float2* stage_m = nullptr;   // [L]    device staging for user-layout images
 
   // tensor-core path (sense_tc.cu)
-  int tc_grid = 0;                 // persistent CTAs (one per SM)
+  int tc_grid = 0;                 // persistent CTAs launched (<= pairs of blocks)
+  int tc_grid_req = 0;             // requested CTAs (one per SM by default)
   int tc_seg_len = 4;              // drain the TMEM accumulators every this many pairs
   int tc_slots_e = 1, tc_slots_a = 1;
   int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E

@@ -330,6 +330,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t D1 = tmem, D2 = tmem + 2 * CP;
+  // Tensor memory is not cleared between kernels and may hold non-finite values left by
+  // an earlier kernel; an MMA that starts an accumulation must not see them, so the
+  // accumulator columns [0, 4 CP) are zeroed before the first MMA (warpgroup g zeroes
+  // columns [g CP, (g+1) CP) of its lane quarter).
+  if (warp < NGEN_WARPS) {
+    const uint32_t zr[4] = {0u, 0u, 0u, 0u};
+    const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (warp >> 2) * CP;
+#pragma unroll
+    for (int c = 0; c < CP; c += 4) tmem_st4(base + c, zr);
+    tmem_st_wait();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   // A run is a maximal range of pairs with the same row block (one output slot); it is
   // cut into segments of at most F pairs. After each segment the FP32 accumulators are
@@ -854,6 +868,10 @@ static void tc_free_layout(sense_plan_s* P) {
 // number of partial slots; partial buffers sized for the largest slot count.
 static int tc_layout(sense_plan_s* P) {
   tc_free_layout(P);
+  // Never more CTAs than (row block, streamed block) pairs: with every CTA range
+  // non-empty, all CTAs between the first and the last contributor of a row block write
+  // their partial slot, so the reduction never reads a slot nobody wrote.
+  P->tc_grid = (int)std::min<long long>(P->tc_grid, (long long)P->nsb * P->nvb);
   std::vector<int> fe, ne, fa, na;
   stream_k_layout(P->nsb, P->nvb, P->tc_grid, fe, ne, &P->tc_slots_e);
   stream_k_layout(P->nvb, P->nsb, P->tc_grid, fa, na, &P->tc_slots_a);
@@ -879,6 +897,7 @@ static int tc_layout(sense_plan_s* P) {
 }
 
 int tc_setup(sense_plan_s* P) {
+  P->tc_grid_req = P->num_sms;
   P->tc_grid = P->num_sms;
   int rc;
   if ((rc = tc_layout(P)) != SENSE_OK) return rc;
@@ -912,8 +931,9 @@ int tc_set_tuning(sense_plan_s* P, int seg_len, int grid) {
     return set_error(SENSE_EINVAL, "seg_len must be 1..64 and grid 0..64 x SMs");
   const int g = grid == 0 ? P->num_sms : grid;
   P->tc_seg_len = seg_len;
-  if (g != P->tc_grid) {
+  if (g != P->tc_grid_req) {
     SENSE_CUDA_TRY(cudaDeviceSynchronize());
+    P->tc_grid_req = g;
     P->tc_grid = g;
     return tc_layout(P);
   }
