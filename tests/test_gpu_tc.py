@@ -112,6 +112,31 @@ def test_tc_results_are_deterministic(case):
         assert bool((a == b).all())
 
 
+@pytest.mark.parametrize("matrix,n_samples", [(20, 1000), (12, 300), (40, 5000)])
+def test_tc_no_reads_of_unwritten_device_memory(matrix, n_samples):
+    """Freshly allocated device memory is poisoned with NaN first (allocate, fill, hand back
+    to the driver), so any read of a workspace element that no kernel wrote shows up. Small
+    problems (fewer block pairs than SMs) once summed partial slots of CTAs with no work."""
+    import torch
+    from paper_2604_09233_gb300 import native
+    dev = torch.device("cuda:0")
+    poison = torch.full((1 << 28,), float("nan"), dtype=torch.float32, device=dev)  # 1 GiB
+    del poison
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    wl = synthetic.small_2d(seed=2, matrix=matrix, n_coils=5, n_samples=n_samples, order=1)
+    ref_s = oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true)
+    ref_q = oracle.normal(wl.Kmat, wl.Rmat, wl.S, wl.m_true)
+    with native.Plan(wl.Kmat, wl.Rmat, wl.S) as plan:
+        m = _t(wl.m_true, dev)
+        for prec in (SPLIT, SINGLE, 0):
+            s = plan.encode(m, prec=prec).cpu().numpy()
+            q = plan.normal(m, prec=prec).cpu().numpy()
+            tol = TOL.get(prec, 1e-5)
+            assert np.isfinite(s).all() and np.isfinite(q).all()
+            assert _rel(s, ref_s) <= tol and _rel(q, ref_q) <= tol
+
+
 @pytest.fixture(scope="module")
 def target():
     import torch
