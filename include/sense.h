@@ -149,6 +149,26 @@ int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opt
  * wins. Host-only. *corner = -1 when n < 3. Errors: EINVAL. */
 int sense_lcurve_corner(const double* history, int32_t n, int32_t* corner);
 
+/* s = E m for callers that cannot allocate device memory (the paper has no counterpart).
+ * Hosts that reserve all GPU memory at start-up and forbid later allocation, and callers
+ * whose device memory is owned by another framework's allocator, can neither create a plan
+ * nor let a call allocate. This entry point takes the problem directly and allocates
+ * nothing: its only scratch (the partial sums of the voxel-split FP32 encode) is a fixed
+ * 16 MiB array inside the library, which every GPU that loads the library holds until the
+ * process exits. Phases are evaluated per pair in FP64 (no plan, no anchors), the rest as
+ * in the FP32 path.
+ *   Kmat [K][P1] float64, Rmat [P1][L] float64, S [L][C] complex64, j [L] float32 or NULL,
+ *   m [L] complex64: DEVICE inputs; s [K][C] complex64: DEVICE output (caller-owned).
+ * Limits: C <= 64, P1 <= 24, K x (C rounded up to 8/16/32/64) <= 2^21; larger sizes are
+ * rejected with SENSE_EINVAL and a message. The first call on a device looks up the
+ * array's device address (with that device current); make that first call before any
+ * stream capture. All calls share the array, which keeps the last call's partial sums;
+ * calls that overlap on the GPU (other streams, other host threads) race on it.
+ * Asynchronous on `stream`. Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const double* Kmat,
+                         const double* Rmat, const float* S, const float* j, const float* m,
+                         float* s, void* stream);
+
 /* Tuning ------------------------------------------------------------------------------
  * (no counterpart in the paper: execution parameters of the tensor-core kernels)
  *   seg_len  the tensor-core passes accumulate at most this many 128 x 128 (sample, voxel)

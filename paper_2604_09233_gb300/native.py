@@ -28,7 +28,7 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_encode", "sense_adjoint", "sense_normal_op", "sense_cg_solve",
             "sense_lcurve_corner", "sense_strerror", "sense_last_error", "sense_plan_profile",
             "sense_plan_stats", "sense_diag_sincos_rate", "sense_plan_get_tuning",
-            "sense_plan_set_tuning", "sense_plan_sync"]
+            "sense_plan_set_tuning", "sense_plan_sync", "sense_encode_noalloc"]
 
 
 class SenseError(RuntimeError):
@@ -87,6 +87,7 @@ def _load():
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
         "sense_plan_sync": ([vp, vp], ctypes.c_int),
+        "sense_encode_noalloc": ([i64, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "sense_plan_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
@@ -210,6 +211,23 @@ def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refi
                                _stream(ss, sx, explicit=stream)), "sense_cg_solve")
     out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
     return out, (None if hist is None else hist[: info.iters + 1])
+
+
+def sense_encode_noalloc(Kmat, Rmat, S, m, s, j=None, stream=None):
+    """s = E m without any device allocation by the library (see include/sense.h). All
+    arrays are CUDA tensors: Kmat [K][P1] float64, Rmat [P1][L] float64, S [L][C]
+    complex64, m [L] complex64, s [K][C] complex64 (output), j [L] float32 or None."""
+    K, P1 = Kmat.shape
+    L = Rmat.shape[1]
+    C = S.shape[1]
+    pk, _, sk = _ptr(Kmat, np.float64)
+    pr, _, _ = _ptr(Rmat, np.float64)
+    pS, _, _ = _ptr(S)
+    pm, _, _ = _ptr(m)
+    ps, _, _ = _ptr(s)
+    pj = None if j is None else _ptr(j, np.float32)[0]
+    _check(_lib.sense_encode_noalloc(int(L), int(K), int(C), int(P1), pk, pr, pS, pj, pm, ps,
+                                     _stream(sk, explicit=stream)), "sense_encode_noalloc")
 
 
 def sense_plan_sync(plan, stream=None):
