@@ -149,6 +149,45 @@ int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opt
  * wins. Host-only. *corner = -1 when n < 3. Errors: EINVAL. */
 int sense_lcurve_corner(const double* history, int32_t n, int32_t* corner);
 
+/* Differentiation ----------------------------------------------------------------------
+ * (no counterpart in the paper, which only solves; these serve B0-map refinement and
+ * training through the reconstruction)
+ * Gradients follow the convention dL/dRe(v) + i dL/dIm(v) of a real loss L.
+ *
+ * B0 gradient primitive. Row 0 of R is the B0 map omega (rad/s) and column 0 of K the
+ * sample time t, so d phi / d omega(l) = t_kappa (Eq. 4). This call computes
+ *     grad_omega(l) = Im( conj(a(l)) * (E^H (t o y))(l) )      [L] float, user voxel order
+ * and, when z is not NULL, z = E^H y ([L] complex64). It is the backward of both operators:
+ *   y_out = E m   with upstream g:  a = m, y = g  ->  dL/domega, and z = dL/dm;
+ *   x_out = E^H y with upstream h:  a = h, y = y  ->  dL/domega (dL/dy = E h: sense_encode).
+ * a [L] complex64, y [K][C] complex64; host or device pointers. The gradient is that of the
+ * operator the plan holds (its current B0 map). Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+int sense_grad_b0(sense_plan plan, int32_t prec, const float* a, const float* y, float* z,
+                  float* grad_omega, void* stream);
+
+/* Checkpointed CG solve for reverse-mode differentiation. Runs exactly sense_cg_solve
+ * (refine_every must be 0) and writes into ckpt (caller-owned device memory, 16-byte
+ * aligned, at least sense_cg_ckpt_bytes() bytes) the residual, search direction and
+ * scalars before every ckpt_every-th iteration plus the final scalars, so that
+ * sense_cg_backward can replay one segment of ckpt_every iterations at a time: memory is
+ * O(max_iter / ckpt_every) vectors for the checkpoints plus ckpt_every vectors (and
+ * ckpt_every E p products) held by the plan during the backward.
+ * sense_cg_ckpt_bytes returns the size, or a negative error code (EINVAL). */
+int64_t sense_cg_ckpt_bytes(sense_plan plan, int32_t max_iter, int32_t ckpt_every);
+int sense_cg_solve_ckpt(sense_plan plan, const float* s, float* x, const sense_cg_opts* opts,
+                        int32_t ckpt_every, void* ckpt, int64_t ckpt_bytes,
+                        sense_cg_info* info, void* stream);
+
+/* Reverse mode through the solve recorded in ckpt: given xbar = dL/dx ([L] complex64) for
+ * the returned x, writes sbar = dL/ds ([K][C] complex64) and/or omega_bar = dL/domega
+ * ([L] float, user voxel order); either output may be NULL, not both. s must be the data
+ * of that solve and the plan must hold the same B0 map. The step lengths are differentiated
+ * (the iterate is a nonlinear function of s and omega); the stopping decision is not.
+ * Synchronises the stream to read the checkpoint header. Errors: EINVAL (ckpt not written
+ * by sense_cg_solve_ckpt on this plan), ENOMEM, ECUDA, ETIMEOUT. */
+int sense_cg_backward(sense_plan plan, const float* s, const void* ckpt, int64_t ckpt_bytes,
+                      const float* xbar, float* sbar, float* omega_bar, void* stream);
+
 /* s = E m for callers that cannot allocate device memory (the paper has no counterpart).
  * Hosts that reserve all GPU memory at start-up and forbid later allocation, and callers
  * whose device memory is owned by another framework's allocator, can neither create a plan

@@ -11,6 +11,7 @@ Functions and the passages they follow:
   normal       E^H E m (Fig. 2 Alg. 1 step 8)
   cg           Fig. 2 Alg. 1 steps 3-18
   grad_omega   chain rule of Eq. 4 w.r.t. row 0 of R (the B0 map)
+  grad_omega_adjoint  chain rule of Eq. 5 w.r.t. row 0 of R (backward of x = E^H y)
   lcurve_corner  maximum-curvature point of the L-curve (log residual norm vs log
                  solution norm over CG iterations), the stopping rule the paper evaluates
 
@@ -26,6 +27,7 @@ from .oracle import (  # noqa: F401
     normal,
     cg,
     grad_omega,
+    grad_omega_adjoint,
     lcurve_corner,
     num_threads,
     set_num_threads,

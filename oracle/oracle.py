@@ -55,6 +55,8 @@ def load():
         lib.or_cg.restype = _int
         lib.or_grad_omega.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
                                       _ptr]
+        lib.or_grad_omega_adjoint.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr,
+                                              _ptr, _ptr, _ptr]
         _lib = lib
         return lib
 
@@ -155,6 +157,17 @@ def grad_omega(Kmat, Rmat, S, m, g, j=None):
     out = np.empty(L, np.float64)
     load().or_grad_omega(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(m), _p(g),
                          _p(out))
+    return out
+
+
+def grad_omega_adjoint(Kmat, Rmat, S, y, h, j=None):
+    """d Loss / d R[0,:] through x = E^H y, given h = dLoss/dRe(x) + i dLoss/dIm(x)."""
+    Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
+    y = _c(y, np.complex128).reshape(K, C)
+    h = _c(h, np.complex128)
+    out = np.empty(L, np.float64)
+    load().or_grad_omega_adjoint(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(y), _p(h),
+                                 _p(out))
     return out
 
 

@@ -196,6 +196,27 @@ int or_cg(int64_t L, int64_t K, int C, int P1, const double* Km, const double* R
  *     dLoss/domega(l) = sum_{kappa,lam} Re( conj(g(kappa,lam)) * dy(kappa,lam)/domega(l) ),
  *     dy(kappa,lam)/domega(l) = i K(kappa,0) S(l,lam) j(l) m(l) e^{i phi(kappa,l)}
  * (the chain rule of Eq. 4; K(kappa,0) = t_kappa multiplies R(0,l) = B0(r_l)). */
+/* Gradient of a real loss through x = E^H y with respect to row 0 of R, given
+ * h = dLoss/dRe(x) + i dLoss/dIm(x) ([L]):
+ *     dLoss/domega(l) = Re( conj(h(l)) * dx(l)/domega(l) ),
+ *     dx(l)/domega(l) = j(l) sum_lam conj(S(l,lam)) sum_kappa (-i K(kappa,0)) e^{-i phi(kappa,l)} y(kappa,lam)
+ * (the chain rule of Eq. 5; x(l) depends on omega(l) alone). */
+void or_grad_omega_adjoint(int64_t L, int64_t K, int C, int P1, const double* Km,
+                           const double* Rm, const cplx* S, const double* j, const cplx* y,
+                           const cplx* h, double* grad) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t l = 0; l < L; ++l) {
+    cplx dx = 0.0;
+    for (int64_t kappa = 0; kappa < K; ++kappa) {
+      const cplx e = cexp(-I * phase_of(Km, Rm, L, P1, kappa, l));
+      for (int lam = 0; lam < C; ++lam)
+        dx += conj(S[l * C + lam]) * (-I * Km[kappa * P1 + 0]) * e * y[kappa * C + lam];
+    }
+    dx *= (j ? j[l] : 1.0);
+    grad[l] = creal(conj(h[l]) * dx);
+  }
+}
+
 void or_grad_omega(int64_t L, int64_t K, int C, int P1, const double* Km, const double* Rm,
                    const cplx* S, const double* j, const cplx* m, const cplx* g,
                    double* grad) {

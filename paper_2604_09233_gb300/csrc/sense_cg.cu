@@ -8,58 +8,9 @@
 #include <vector>
 
 #include "sense_internal.cuh"
+#include "sense_reduce.cuh"
 
 namespace sense {
-
-constexpr int VB = 256;  // threads per block of the vector kernels
-
-// ---------------------------------------------------------------------------------------
-// Block reduction of N doubles + last-block completion.
-// ---------------------------------------------------------------------------------------
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double* sh /* [N][VB/32] */) {
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0)
-#pragma unroll
-    for (int j = 0; j < N; ++j) sh[j * (VB / 32) + w] = v[j];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      double a = 0.0;
-      for (int i = 0; i < VB / 32; ++i) a += sh[j * (VB / 32) + i];
-      v[j] = a;
-    }
-}
-
-// Writes this block's sums; returns true (in thread 0 only) if this block finished last,
-// in which case tot[] holds the totals over all blocks in block order.
-template <int N>
-__device__ __forceinline__ bool finish_sums(double (&v)[N], double* part, unsigned* counter,
-                                            double (&tot)[N]) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < N; ++j) part[blockIdx.x * N + j] = v[j];
-    __threadfence();
-    const unsigned done = atomicAdd(counter, 1u);
-    last = (done == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return false;
-  __threadfence();
-#pragma unroll
-  for (int j = 0; j < N; ++j) tot[j] = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b)
-#pragma unroll
-    for (int j = 0; j < N; ++j) tot[j] += ((volatile double*)part)[b * N + j];
-  *counter = 0u;
-  return true;
-}
 
 __device__ __forceinline__ bool stopped(const double* scal) { return scal[SC_STOP] != 0.0; }
 
@@ -312,7 +263,7 @@ __global__ void cg_p_kernel(float2* p, const float2* __restrict__ r, int64_t Lp,
 // ---------------------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------------------
-static int grid_for(sense_plan_s* P, int64_t n) {
+int grid_for(sense_plan_s* P, int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + VB - 1) / VB, 8 * P->num_sms));
 }
 
@@ -353,7 +304,7 @@ int reduce_xpart(sense_plan_s* P, float2* q, const double* stop, cudaStream_t st
   return SENSE_OK;
 }
 
-static int check_prec(int prec) {
+int check_prec(int prec) {
   if (prec == SENSE_PREC_FP32 || prec == SENSE_PREC_TC_FP16 || prec == SENSE_PREC_TC_SPLIT)
     return SENSE_OK;
   return set_error(SENSE_EINVAL, "unknown precision mode");
@@ -382,15 +333,42 @@ int adjoint_internal(sense_plan_s* P, int prec, const float2* Y, float2* q, cons
   return reduce_xpart(P, q, stop, st);
 }
 
+// one launch each of steps 9-12, 11-14 and 15 on the plan's CG vectors
+int cg_step_alpha(sense_plan_s* P, cudaStream_t st) {
+  cg_alpha_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->vp, P->vq, P->Lp, P->red, P->counter,
+                                                     P->scal);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  return SENSE_OK;
+}
+
+int cg_step_update(sense_plan_s* P, double* hist, cudaStream_t st) {
+  cg_update_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->vx, P->vr, P->vp, P->vq, P->vb, P->Lp,
+                                                      P->red, P->counter, P->scal, hist);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  return SENSE_OK;
+}
+
+int cg_step_p(sense_plan_s* P, cudaStream_t st) {
+  cg_p_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->vp, P->vr, P->Lp, P->scal);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  return SENSE_OK;
+}
+
+// Y_int = E p (internal data layout)
+int encode_internal(sense_plan_s* P, int prec, const float2* p, float2* Y, cudaStream_t st) {
+  int rc;
+  if (prec != SENSE_PREC_FP32) return tc_encode(P, prec, p, Y, nullptr, false, nullptr, st);
+  if ((rc = fp32_encode_partials(P, p, nullptr, st)) != SENSE_OK) return rc;
+  return reduce_y(P, Y, nullptr, nullptr, st);
+}
+
 // Argument staging: a host pointer is copied into a plan buffer (inputs) or written back
 // after the work (outputs).
-struct Staged {
-  const void* user;
-  void* dev;
-  bool host;
-};
 
-static int stage_in(const void* user, void* buf, size_t bytes, cudaStream_t st, Staged* s) {
+int stage_in(const void* user, void* buf, size_t bytes, cudaStream_t st, Staged* s) {
   s->user = user;
   s->host = !is_device_pointer(user);
   s->dev = s->host ? buf : const_cast<void*>(user);
@@ -399,7 +377,7 @@ static int stage_in(const void* user, void* buf, size_t bytes, cudaStream_t st, 
   return SENSE_OK;
 }
 
-static Staged stage_out(void* user, void* buf) {
+Staged stage_out(void* user, void* buf) {
   Staged s;
   s.user = user;
   s.host = !is_device_pointer(user);
@@ -407,14 +385,14 @@ static Staged stage_out(void* user, void* buf) {
   return s;
 }
 
-static int finish_out(const Staged& s, size_t bytes, cudaStream_t st) {
+int finish_out(const Staged& s, size_t bytes, cudaStream_t st) {
   if (!s.host) return SENSE_OK;
   SENSE_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(s.user), s.dev, bytes, cudaMemcpyDeviceToHost, st));
   SENSE_CUDA_TRY(cudaStreamSynchronize(st));
   return SENSE_OK;
 }
 
-static int check_plan(sense_plan_s* P) {
+int check_plan(sense_plan_s* P) {
   if (!P) return set_error(SENSE_EINVAL, "null plan");
   int dev = -1;
   SENSE_CUDA_TRY(cudaGetDevice(&dev));
@@ -493,7 +471,14 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   if (opts->max_iter < 0 || !(opts->rel_tol >= 0.0) || opts->refine_every < 0)
     return set_error(SENSE_EINVAL, "max_iter, rel_tol and refine_every must be >= 0");
   TRY(check_prec(opts->prec));
-  cudaStream_t st = (cudaStream_t)stream;
+  return cg_run(P, s, x, opts, history, info, 0, nullptr, (cudaStream_t)stream);
+}
+
+namespace sense {
+
+int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
+           double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
+           cudaStream_t st) {
   const int N = opts->max_iter;
   if (N + 1 > P->max_hist) {
     cudaFree(P->hist);
@@ -527,15 +512,11 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   count_launch(P);
   const double* stop = P->scal + SC_STOP;
   for (int n = 0; n < N; ++n) {
+    if (ckpt_every > 0 && n % ckpt_every == 0) TRY(ckpt_save(P, ckpt, n / ckpt_every, st));
     // step 8
     TRY(apply_normal_internal(P, opts->prec, P->vp, P->vq, stop, st));
-    cg_alpha_kernel<<<vb, VB, 0, st>>>(P->vp, P->vq, P->Lp, P->red, P->counter, P->scal);
-    SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
-    cg_update_kernel<<<vb, VB, 0, st>>>(P->vx, P->vr, P->vp, P->vq, P->vb, P->Lp, P->red,
-                                        P->counter, P->scal, P->hist);
-    SENSE_CUDA_TRY(cudaGetLastError());
-    count_launch(P);
+    TRY(cg_step_alpha(P, st));
+    TRY(cg_step_update(P, P->hist, st));
     if (opts->prec != SENSE_PREC_FP32 && opts->refine_every > 0 &&
         (n + 1) % opts->refine_every == 0 && n + 1 < N) {
       // residual replacement with the FP32 operator
@@ -545,10 +526,9 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
       SENSE_CUDA_TRY(cudaGetLastError());
       count_launch(P);
     }
-    cg_p_kernel<<<vb, VB, 0, st>>>(P->vp, P->vr, P->Lp, P->scal);
-    SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
+    TRY(cg_step_p(P, st));
   }
+  if (ckpt_every > 0) TRY(ckpt_final(P, ckpt, st));
   // step 18
   TRY(scatter_image(P, P->vx, (float2*)out.dev, opts->apply_j != 0, st));
   if (history || info) {
@@ -572,3 +552,5 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   const bool synced = history || info || out.host;
   return synced && opts->prec != SENSE_PREC_FP32 ? tc_check_error(P) : SENSE_OK;
 }
+
+}  // namespace sense

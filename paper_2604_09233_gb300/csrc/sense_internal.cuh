@@ -118,6 +118,18 @@ struct sense_plan_s {
   float2* Xpart_tc = nullptr;      // [tc_slots_a][Lp]
   int* tc_err = nullptr;           // time-out word written by the tensor-core kernels
 
+  // gradient workspace (sense_grad.cu), allocated on first use
+  float2* Yg = nullptr;            // [Kp][Cp] E of an adjoint vector
+  float2* Yt = nullptr;            // [Kp][Cp] t-weighted data
+  float2* vt = nullptr;            // [Lp] E^H (t o y)
+  float* gw = nullptr;             // [Lp] d/d omega accumulator, plan order
+  float2 *gx = nullptr, *gr = nullptr, *gp = nullptr, *gq = nullptr;  // [Lp] CG adjoints
+  double* gsc = nullptr;           // [8] backward scalars
+  int seg_cap = 0;                 // iterations the segment store holds
+  float2 *seg_p = nullptr, *seg_q = nullptr, *seg_r = nullptr;  // [seg_cap][Lp]
+  float2* seg_Y = nullptr;         // [seg_cap][Kp][Cp]  E p_n
+  double* seg_sc = nullptr;        // [seg_cap][SC_COUNT]
+
   // diagnostics (sense_diag.cu)
   int64_t n_launch = 0;
   bool prof_on = false;
@@ -178,9 +190,37 @@ void prof_free(sense_plan_s* P);
 inline void count_launch(sense_plan_s* P, int n = 1) { P->n_launch += n; }
 
 // CG (sense_cg.cu) --------------------------------------------------------------------
+// Host-pointer arguments are staged through plan buffers: inputs copied in before the work,
+// outputs copied back (synchronously) after it.
+struct Staged {
+  const void* user;
+  void* dev;
+  bool host;
+};
+int stage_in(const void* user, void* buf, size_t bytes, cudaStream_t st, Staged* s);
+Staged stage_out(void* user, void* buf);
+int finish_out(const Staged& s, size_t bytes, cudaStream_t st);
+int check_plan(sense_plan_s* P);
+int check_prec(int prec);
+int grid_for(sense_plan_s* P, int64_t n);
+// One CG solve; with ckpt_every > 0 the state (r, p, scalars) before every ckpt_every-th
+// iteration and the final scalars are written to ckpt (layout of sense_grad.cu).
+int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
+           double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
+           cudaStream_t st);
+int encode_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int,
+                    cudaStream_t st);
+int cg_step_alpha(sense_plan_s* P, cudaStream_t st);
+int cg_step_update(sense_plan_s* P, double* hist, cudaStream_t st);
+int cg_step_p(sense_plan_s* P, cudaStream_t st);
 int apply_normal_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* q_plan,
                           const double* stop, cudaStream_t st);
 int adjoint_internal(sense_plan_s* P, int prec, const float2* Y_int, float2* q_plan,
                      const double* stop, cudaStream_t st);
+
+// gradients and checkpoints (sense_grad.cu) ------------------------------------------------
+void grad_free(sense_plan_s* P);
+int ckpt_save(sense_plan_s* P, uint8_t* ckpt, int64_t slot, cudaStream_t st);
+int ckpt_final(sense_plan_s* P, uint8_t* ckpt, cudaStream_t st);
 
 }  // namespace sense

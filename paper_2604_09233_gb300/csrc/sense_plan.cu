@@ -338,6 +338,7 @@ static void plan_free_all(sense_plan_s* P) {
   cudaFree(P->vm); cudaFree(P->scal); cudaFree(P->hist); cudaFree(P->red);
   cudaFree(P->counter); cudaFree(P->stage_s); cudaFree(P->stage_m);
   tc_free(P);
+  grad_free(P);
   prof_free(P);
   delete P;
 }

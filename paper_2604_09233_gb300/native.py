@@ -28,7 +28,8 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_encode", "sense_adjoint", "sense_normal_op", "sense_cg_solve",
             "sense_lcurve_corner", "sense_strerror", "sense_last_error", "sense_plan_profile",
             "sense_plan_stats", "sense_diag_sincos_rate", "sense_plan_get_tuning",
-            "sense_plan_set_tuning", "sense_plan_sync", "sense_encode_noalloc"]
+            "sense_plan_set_tuning", "sense_plan_sync", "sense_encode_noalloc",
+            "sense_grad_b0", "sense_cg_ckpt_bytes", "sense_cg_solve_ckpt", "sense_cg_backward"]
 
 
 class SenseError(RuntimeError):
@@ -88,6 +89,11 @@ def _load():
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
         "sense_plan_sync": ([vp, vp], ctypes.c_int),
         "sense_encode_noalloc": ([i64, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "sense_grad_b0": ([vp, i32, vp, vp, vp, vp, vp], ctypes.c_int),
+        "sense_cg_ckpt_bytes": ([vp, i32, i32], i64),
+        "sense_cg_solve_ckpt": ([vp, vp, vp, ctypes.POINTER(CGOpts), i32, vp, i64,
+                                 ctypes.POINTER(CGInfo), vp], ctypes.c_int),
+        "sense_cg_backward": ([vp, vp, vp, i64, vp, vp, vp, vp], ctypes.c_int),
         "sense_plan_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
@@ -120,7 +126,7 @@ def _ptr(a, dtype=np.complex64):
             if not a.is_contiguous():
                 raise ValueError("tensor must be contiguous")
             want = {np.complex64: torch.complex64, np.float64: torch.float64,
-                    np.float32: torch.float32}[dtype]
+                    np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
             if a.dtype != want:
                 raise TypeError(f"expected {want}, got {a.dtype}")
             stream = torch.cuda.current_stream(a.device).cuda_stream if a.is_cuda else None
@@ -228,6 +234,49 @@ def sense_encode_noalloc(Kmat, Rmat, S, m, s, j=None, stream=None):
     pj = None if j is None else _ptr(j, np.float32)[0]
     _check(_lib.sense_encode_noalloc(int(L), int(K), int(C), int(P1), pk, pr, pS, pj, pm, ps,
                                      _stream(sk, explicit=stream)), "sense_encode_noalloc")
+
+
+def sense_grad_b0(plan, prec, a, y, grad_omega, z=None, stream=None):
+    """grad_omega = Im(conj(a) * E^H(t o y)) ([L] float32) and, if z is given, z = E^H y."""
+    pa, _, sa = _ptr(a)
+    py, _, sy = _ptr(y)
+    pg, _, sg = _ptr(grad_omega, np.float32)
+    pz, _, _ = _ptr(z)
+    _check(_lib.sense_grad_b0(plan, int(prec), pa, py, pz, pg,
+                              _stream(sa, sy, sg, explicit=stream)), "sense_grad_b0")
+
+
+def sense_cg_ckpt_bytes(plan, max_iter, ckpt_every):
+    n = _lib.sense_cg_ckpt_bytes(plan, int(max_iter), int(ckpt_every))
+    if n < 0:
+        raise SenseError(int(n), "sense_cg_ckpt_bytes")
+    return int(n)
+
+
+def sense_cg_solve_ckpt(plan, s, x, ckpt, max_iter, ckpt_every, prec=SENSE_PREC_FP32,
+                        rel_tol=0.0, apply_j=True, stream=None):
+    """CG solve that records checkpoints into ckpt (a uint8 CUDA tensor of at least
+    sense_cg_ckpt_bytes bytes). Returns the info dict."""
+    ps, _, ss = _ptr(s)
+    px, _, sx = _ptr(x)
+    pc, kc, _ = _ptr(ckpt, np.uint8)
+    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), 0, 1 if apply_j else 0)
+    info = CGInfo()
+    _check(_lib.sense_cg_solve_ckpt(plan, ps, px, ctypes.byref(opts), int(ckpt_every), pc,
+                                    int(kc.numel()), ctypes.byref(info),
+                                    _stream(ss, sx, explicit=stream)), "sense_cg_solve_ckpt")
+    return dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
+
+
+def sense_cg_backward(plan, s, ckpt, xbar, sbar=None, omega_bar=None, stream=None):
+    """Reverse mode through the solve recorded in ckpt: sbar = dL/ds, omega_bar = dL/domega."""
+    ps, _, ss = _ptr(s)
+    pc, kc, _ = _ptr(ckpt, np.uint8)
+    pxb, _, sxb = _ptr(xbar)
+    psb, _, _ = _ptr(sbar)
+    pwb, _, _ = _ptr(omega_bar, np.float32)
+    _check(_lib.sense_cg_backward(plan, ps, pc, int(kc.numel()), pxb, psb, pwb,
+                                  _stream(ss, sxb, explicit=stream)), "sense_cg_backward")
 
 
 def sense_plan_sync(plan, stream=None):

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "sense.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(sense_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(sense_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")

@@ -216,6 +216,29 @@ def test_grad_omega_matches_central_differences(small):
         assert abs(fd - grad[l]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max()), l
 
 
+def test_grad_omega_adjoint_matches_central_differences(small):
+    """x = E^H y: the B0 gradient of a loss of x, against central differences."""
+    wl = small
+    rng = np.random.default_rng(5)
+    y = _crandn(rng, wl.K, wl.C)
+    w = _crandn(rng, wl.L)
+
+    def loss(Rm):
+        x = oracle.adjoint(wl.Kmat, Rm, wl.S, y, j=wl.j)
+        return np.vdot(w, x).real + 0.25 * np.vdot(x, x).real
+
+    x0 = oracle.adjoint(wl.Kmat, wl.Rmat, wl.S, y, j=wl.j)
+    h_up = w + 0.5 * x0                      # dLoss/dRe(x) + i dLoss/dIm(x)
+    grad = oracle.grad_omega_adjoint(wl.Kmat, wl.Rmat, wl.S, y, h_up, j=wl.j)
+    h = 1e-2
+    for l in (0, 17, 60, 143):
+        Rp, Rn = wl.Rmat.copy(), wl.Rmat.copy()
+        Rp[0, l] += h
+        Rn[0, l] -= h
+        fd = (loss(Rp) - loss(Rn)) / (2 * h)
+        assert abs(fd - grad[l]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max()), l
+
+
 def test_lcurve_corner_on_parabola_vertex():
     """(a, b) = (x, x^2) traversed right to left: curvature peaks (value 2) at the vertex."""
     xs = np.linspace(2.0, -1.0, 31)           # vertex at index 20
