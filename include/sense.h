@@ -208,6 +208,44 @@ int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const doub
                          const double* Rmat, const float* S, const float* j, const float* m,
                          float* s, void* stream);
 
+/* Batched reconstruction -----------------------------------------------------------------
+ * (no counterpart in the paper, which reconstructs one slice or volume at a time)
+ * A batch holds n independent problems of uneven size (voxels, samples, coils, basis rows)
+ * and solves them together: each E and E^H of a batch iteration is one persistent launch
+ * whose CTAs claim (instance, row block, chunk) work items from a device queue, skipping
+ * instances whose CG has stopped; one CG iteration of the whole batch is captured once in a
+ * CUDA graph and replayed. All instances share the batch-wide padded coil count and delta
+ * row count (zero padding), so the batch costs at most what its largest member's layout
+ * costs per (sample, voxel) pair. Tensor-core precisions only (TC_FP16, TC_SPLIT).
+ *
+ * sense_batch_create: probs[n] as for sense_plan_create (host arrays, copied). The batch
+ *   owns one plan per instance; sense_batch_plan returns it (borrowed: do not destroy) for
+ *   single-instance calls. Errors as sense_plan_create, EINVAL for n < 1.
+ * sense_batch_info: out = {n, padded coils, delta rows, chunk}.
+ * sense_batch_normal_op: out[b] = E_b^H E_b m[b] for every b ([L_b] complex64, device).
+ * sense_batch_cg_solve: sense_cg_solve for every instance with the same options (history
+ *   not recorded, refine_every must be 0); s[b] [K_b][C_b] and x[b] [L_b] device pointers,
+ *   info[n] (nullable; when given the call synchronises and reports ETIMEOUT). Instances
+ *   stop individually (rel_tol or max_iter). The first call per precision captures the
+ *   iteration graph; concurrent solves on one batch race.
+ * sense_batch_set_tuning: streamed blocks per work item (chunk, 1..4096) and accumulator
+ *   segment length (1..64); defaults 16 and 4.
+ * sense_batch_autotune: times the batched E^H E for chunk in {8,16,32,64} x seg_len in
+ *   {2,4} and keeps the fastest; returns it and its time (ms) through the non-null outputs.
+ */
+typedef struct sense_batch_s* sense_batch;
+int sense_batch_create(const sense_problem* probs, int32_t n, sense_batch* out);
+int sense_batch_destroy(sense_batch batch);
+int sense_batch_plan(sense_batch batch, int32_t i, sense_plan* out);
+int sense_batch_info(sense_batch batch, int32_t out[4]);
+int sense_batch_normal_op(sense_batch batch, int32_t prec, const float* const* m,
+                          float* const* out, void* stream);
+int sense_batch_cg_solve(sense_batch batch, const float* const* s, float* const* x,
+                         const sense_cg_opts* opts, sense_cg_info* info, void* stream);
+int sense_batch_set_tuning(sense_batch batch, int32_t chunk, int32_t seg_len);
+int sense_batch_autotune(sense_batch batch, int32_t prec, int32_t* chunk, int32_t* seg_len,
+                         double* ms);
+
 /* Tuning ------------------------------------------------------------------------------
  * (no counterpart in the paper: execution parameters of the tensor-core kernels)
  *   seg_len  the tensor-core passes accumulate at most this many 128 x 128 (sample, voxel)

@@ -476,6 +476,47 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
 
 namespace sense {
 
+// Steps 1-5 for data s (device, user layout): coil data in the internal layout, ||s||^2,
+// b = E^H s, x = 0, r = p = b, r^H r and the stopping thresholds.
+int cg_begin(sense_plan_s* P, const float2* s, const sense_cg_opts* opts, double* hist,
+             cudaStream_t st) {
+  const int vb = grid_for(P, P->Lp);
+  const int yb = grid_for(P, P->Kp * P->Cp);
+  TRY(load_data(P, s, P->Ydata, st));
+  data_norm_kernel<<<yb, VB, 0, st>>>(P->Ydata, P->Kp * P->Cp, P->red, P->counter, P->scal);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  // step 3: b = E^H sigma (FP32 operator, or the split tensor-core operator when the
+  // iterations use it; FP32 whenever the residual is refined: b enters every replaced
+  // residual)
+  const int prec_b = (opts->prec == SENSE_PREC_TC_SPLIT && opts->refine_every == 0)
+                         ? SENSE_PREC_TC_SPLIT
+                         : SENSE_PREC_FP32;
+  TRY(adjoint_internal(P, prec_b, P->Ydata, P->vb, nullptr, st));
+  cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
+                                    P->scal, hist, opts->rel_tol, opts->max_iter);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  return SENSE_OK;
+}
+
+// Synchronises st and reads the iteration count and status of the last solve.
+int cg_read_info(sense_plan_s* P, sense_cg_info* info, int* iters, cudaStream_t st) {
+  double sc[SC_COUNT];
+  SENSE_CUDA_TRY(cudaMemcpyAsync(sc, P->scal, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (iters) *iters = (int)sc[SC_ITER];
+  if (info) {
+    info->iters = (int)sc[SC_ITER];
+    info->status = sc[SC_STOP] == 2.0 ? SENSE_EBREAKDOWN
+                   : sc[SC_STOP] == 3.0 ? SENSE_ENONFINITE
+                                        : SENSE_OK;
+    info->rr0 = sc[SC_RR0];
+    info->rr_final = sc[SC_RR];
+  }
+  return SENSE_OK;
+}
+
 int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
            double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
            cudaStream_t st) {
@@ -494,22 +535,7 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
   TRY(stage_in(s, P->stage_s, (size_t)P->K * P->C * 8, st, &in));
   Staged out = stage_out(x, P->stage_m);
   const int vb = grid_for(P, P->Lp);
-  const int yb = grid_for(P, P->Kp * P->Cp);
-  TRY(load_data(P, (const float2*)in.dev, P->Ydata, st));
-  data_norm_kernel<<<yb, VB, 0, st>>>(P->Ydata, P->Kp * P->Cp, P->red, P->counter, P->scal);
-  SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
-  // step 3: b = E^H sigma (FP32 operator, or the split tensor-core operator when the
-  // iterations use it)
-  // (FP32 whenever the residual is refined: b enters every replaced residual)
-  const int prec_b = (opts->prec == SENSE_PREC_TC_SPLIT && opts->refine_every == 0)
-                         ? SENSE_PREC_TC_SPLIT
-                         : SENSE_PREC_FP32;
-  TRY(adjoint_internal(P, prec_b, P->Ydata, P->vb, nullptr, st));
-  cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
-                                    P->scal, P->hist, opts->rel_tol, N);
-  SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
+  TRY(cg_begin(P, (const float2*)in.dev, opts, P->hist, st));
   const double* stop = P->scal + SC_STOP;
   for (int n = 0; n < N; ++n) {
     if (ckpt_every > 0 && n % ckpt_every == 0) TRY(ckpt_save(P, ckpt, n / ckpt_every, st));
@@ -532,21 +558,11 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
   // step 18
   TRY(scatter_image(P, P->vx, (float2*)out.dev, opts->apply_j != 0, st));
   if (history || info) {
-    double sc[SC_COUNT];
-    SENSE_CUDA_TRY(cudaMemcpyAsync(sc, P->scal, sizeof(sc), cudaMemcpyDeviceToHost, st));
-    SENSE_CUDA_TRY(cudaStreamSynchronize(st));
-    const int iters = (int)sc[SC_ITER];
+    int iters = 0;
+    TRY(cg_read_info(P, info, &iters, st));
     if (history)
       SENSE_CUDA_TRY(cudaMemcpy(history, P->hist, (size_t)(iters + 1) * 3 * sizeof(double),
                                 cudaMemcpyDeviceToHost));
-    if (info) {
-      info->iters = iters;
-      info->status = sc[SC_STOP] == 2.0 ? SENSE_EBREAKDOWN
-                     : sc[SC_STOP] == 3.0 ? SENSE_ENONFINITE
-                                          : SENSE_OK;
-      info->rr0 = sc[SC_RR0];
-      info->rr_final = sc[SC_RR];
-    }
   }
   TRY(finish_out(out, (size_t)P->L * 8, st));
   const bool synced = history || info || out.host;

@@ -107,6 +107,7 @@ struct sense_plan_s {
   int tc_grid = 0;                 // persistent CTAs launched (<= pairs of blocks)
   int tc_grid_req = 0;             // requested CTAs (one per SM by default)
   int tc_seg_len = 4;              // drain the TMEM accumulators every this many pairs
+  int min_rt = 0;                  // lower bound on RT (uniform kernels across a batch)
   int tc_slots_e = 1, tc_slots_a = 1;
   int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E
   int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [nvb] stream-K slots of E^H
@@ -138,6 +139,9 @@ struct sense_plan_s {
 };
 
 namespace sense {
+
+// plan creation with lower bounds on the padded coil count and the delta rows (0 = none)
+int plan_create(const sense_problem* prob, int min_cp, int min_rt, sense_plan_s** out);
 
 // error reporting -------------------------------------------------------------------
 int set_error(int code, const std::string& msg);
@@ -208,6 +212,9 @@ int grid_for(sense_plan_s* P, int64_t n);
 int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
            double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
            cudaStream_t st);
+int cg_begin(sense_plan_s* P, const float2* s_dev, const sense_cg_opts* opts, double* hist,
+             cudaStream_t st);
+int cg_read_info(sense_plan_s* P, sense_cg_info* info, int* iters, cudaStream_t st);
 int encode_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int,
                     cudaStream_t st);
 int cg_step_alpha(sense_plan_s* P, cudaStream_t st);

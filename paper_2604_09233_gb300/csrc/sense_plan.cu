@@ -228,7 +228,7 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
     static const int rt_sizes[] = {4, 6, 8, 10, 12, 16, 20};
     P->RT = 20;
     for (int v : rt_sizes)
-      if (v >= P->r) {
+      if (v >= std::max(P->r, P->min_rt)) {
         P->RT = v;
         break;
       }
@@ -348,6 +348,12 @@ static void plan_free_all(sense_plan_s* P) {
 using namespace sense;
 
 extern "C" int sense_plan_create(const sense_problem* prob, sense_plan* out) {
+  return plan_create(prob, 0, 0, out);
+}
+
+namespace sense {
+
+int plan_create(const sense_problem* prob, int min_cp, int min_rt, sense_plan_s** out) {
   if (!prob || !out) return set_error(SENSE_EINVAL, "null problem or output pointer");
   *out = nullptr;
   if (prob->L < 1 || prob->K < 1 || prob->C < 1 || prob->P1 < 1)
@@ -387,6 +393,8 @@ extern "C" int sense_plan_create(const sense_problem* prob, sense_plan* out) {
   P->Lp = (L + TILE - 1) / TILE * TILE;
   P->Kp = (K + TILE - 1) / TILE * TILE;
   P->Cp = C <= 8 ? 8 : C <= 16 ? 16 : C <= 32 ? 32 : 64;
+  P->Cp = std::max(P->Cp, min_cp);
+  P->min_rt = min_rt;
   P->nsb = (int)(P->Kp / TILE);
   P->nvb = (int)(P->Lp / TILE);
   P->Kh.assign(prob->Kmat, prob->Kmat + K * P1);
@@ -429,6 +437,8 @@ extern "C" int sense_plan_create(const sense_problem* prob, sense_plan* out) {
   *out = P;
   return SENSE_OK;
 }
+
+}  // namespace sense
 
 extern "C" int sense_plan_destroy(sense_plan plan) {
   if (!plan) return SENSE_OK;

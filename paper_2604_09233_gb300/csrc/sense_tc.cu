@@ -26,7 +26,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "sense_internal.cuh"
+#include "sense_tc.cuh"
 
 namespace sense {
 namespace tc {
@@ -37,26 +37,6 @@ constexpr int LOAD_WARP = 17;
 constexpr int NTHREADS = 18 * 32;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s
-
-enum Mode { ENC = 0, ADJ = 1 };
-
-struct Params {
-  const float* rowT;     // [n_outer][RT][128] own-dimension deltas (dK for ENC, dR for ADJ)
-  const float* colT;     // [n_inner][RT][128] streamed deltas
-  const float* rowAnc;   // [n_inner][rows_total] (Banc for ENC, Aanc for ADJ)
-  const float* colAnc;   // [n_outer][cols_total] (Aanc for ENC, Banc for ADJ)
-  const uint8_t* Bimg;   // [n_inner][2 halves][NPART][2*CP rows][128 B]
-  const float* bscale;   // [CP] 2^-e unscale per coil
-  const float2* S;       // [rows_total][CP] (ADJ epilogue)
-  float2* out;           // ENC: [slots][rows_total][CP]; ADJ: [slots][rows_total]
-  const int* first_cta;  // [n_outer]
-  int* err;              // device error word (nonzero after a time-out)
-  const double* stop;    // CG stop flag (nullable)
-  long long rows_total, cols_total;
-  long long W;           // n_outer * n_inner
-  int n_outer, n_inner;
-  int seg_len;           // accumulator drain interval (pairs of 128 x 128)
-};
 
 // ---------------------------------------------------------------------------------------
 // PTX wrappers
@@ -282,12 +262,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   float* sRowAnc = sAnc + NBUF * 128;                              // [NBUF][128]
   float2* sRed = (float2*)(sRowAnc + NBUF * 128);                  // [4][128]
   float2* sRacc = sRed + 4 * 128;                                  // [CP/4][512]
-  uint64_t* bars = (uint64_t*)(sRacc + (CP / 4) * NGEN_WARPS * 32); // barriers
+  Meta* sMeta = (Meta*)(sRacc + (CP / 4) * NGEN_WARPS * 32);      // [NBUF]
+  uint64_t* bars = (uint64_t*)(sMeta + NBUF);                      // barriers
   uint64_t* full = bars;                      // [NBUF]
   uint64_t* empty = bars + NBUF;              // [NBUF]
   uint64_t* tfull = bars + 2 * NBUF;          // [SM::NSLOT]
-  uint64_t* tempty = tfull + SM::NSLOT;           // [SM::NSLOT]
-  uint64_t* afull = tempty + SM::NSLOT;           // accumulator full
+  uint64_t* tempty = tfull + SM::NSLOT;       // [SM::NSLOT]
+  uint64_t* afull = tempty + SM::NSLOT;       // accumulator full
   uint64_t* aempty = afull + 1;               // accumulator drained
   uint64_t* drain = aempty + 1;               // final MMA drain
   uint64_t* ered = drain + 1;                 // ADJ epilogue: partial sums written
@@ -297,9 +278,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (p.stop && *p.stop != 0.0) return;
+  const bool queue = p.inst != nullptr;
+  // instance descriptor (kernel parameter space for stream-K, global memory for the queue)
+  auto desc = [&](int b) -> const InstDesc& { return queue ? p.inst[b] : p.d0; };
 
-  const long long G = gridDim.x, i = blockIdx.x;
-  const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
+  const long long i = blockIdx.x;
   const int F = p.seg_len;
 
   if (threadIdx.x == 0) {
@@ -347,32 +330,68 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
   // A run is a maximal range of pairs with the same row block (one output slot); it is
   // cut into segments of at most F pairs. After each segment the FP32 accumulators are
-  // read out of TMEM and added to a per-thread running sum in registers (a short
-  // accumulation chain in the tensor core, FP32 adds across segments); the running sum
-  // is written once per run.
+  // read out of TMEM and added to a per-thread running sum; the running sum is written
+  // once per run. The loader decides the pairs and passes them on in sMeta.
 
   if (warp == LOAD_WARP) {
     // ------------------------------------------------------------------ loader
     if (lane == 0) {
       const uint32_t col_bytes = 128u * RT * 4u;
       long long it = 0;
-      for (long long w = w0; w < w1; ++w, ++it) {
-        const int o = (int)(w / p.n_inner), in = (int)(w % p.n_inner);
+      bool ok = true;
+      // claim the next stage buffer and publish its metadata; with data, also issue the
+      // stage's bulk copies (the full barrier completes when they land)
+      auto push = [&](int b, int o, int in, int flags, int slot) -> bool {
         const int buf = (int)(it % NBUF);
         const uint32_t use = (uint32_t)(it / NBUF);
         if (use > 0 && !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1))
-          break;
+          return false;
+        Meta m;
+        m.inst = b; m.o = o; m.in = in; m.flags = flags; m.slot = slot;
+        m.pad0 = m.pad1 = m.pad2 = 0;
+        sMeta[buf] = m;
         const uint32_t fb = smem_u32(&full[buf]);
-        mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 1024u);
-        bulk_g2s(smem_u32(sB + buf * SM::B_BYTES), p.Bimg + (long long)in * SM::B_BYTES,
-                 SM::B_BYTES, fb);
-        bulk_g2s(smem_u32(sCol + buf * 128 * RT), p.colT + (long long)in * 128 * RT, col_bytes,
-                 fb);
-        bulk_g2s(smem_u32(sAnc + buf * 128), p.colAnc + (long long)o * p.cols_total + in * 128,
-                 512u, fb);
-        bulk_g2s(smem_u32(sRowAnc + buf * 128),
-                 p.rowAnc + (long long)in * p.rows_total + (long long)o * 128, 512u, fb);
+        if (flags & META_END) {
+          mbar_arrive(fb);
+        } else {
+          const InstDesc& d = desc(b);
+          mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 1024u);
+          bulk_g2s(smem_u32(sB + buf * SM::B_BYTES), d.Bimg + (long long)in * SM::B_BYTES,
+                   SM::B_BYTES, fb);
+          bulk_g2s(smem_u32(sCol + buf * 128 * RT), d.colT + (long long)in * 128 * RT,
+                   col_bytes, fb);
+          bulk_g2s(smem_u32(sAnc + buf * 128), d.colAnc + (long long)o * d.cols_total + in * 128,
+                   512u, fb);
+          bulk_g2s(smem_u32(sRowAnc + buf * 128),
+                   d.rowAnc + (long long)in * d.rows_total + (long long)o * 128, 512u, fb);
+        }
+        ++it;
+        return true;
+      };
+      if (!queue) {
+        const long long G = gridDim.x;
+        const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
+        const int n_inner = p.d0.n_inner;
+        for (long long w = w0; w < w1 && ok; ++w) {
+          const int o = (int)(w / n_inner), in = (int)(w % n_inner);
+          const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
+                            ((w + 1 == w1 || in + 1 == n_inner) ? META_LAST : 0);
+          ok = push(0, o, in, flags, (int)(i - p.first_cta[o]));
+        }
+      } else {
+        while (ok) {
+          const unsigned k = atomicAdd(p.next, 1u);
+          if (k >= (unsigned)p.n_items) break;
+          const int4 itm = p.items[k];
+          const InstDesc& d = desc(itm.x);
+          if (d.stop && *(volatile const double*)d.stop != 0.0) continue;
+          const int slot = itm.z / d.chunk;
+          for (int in = itm.z; in < itm.w && ok; ++in)
+            ok = push(itm.x, itm.y, in,
+                      (in == itm.z ? META_FIRST : 0) | (in + 1 == itm.w ? META_LAST : 0), slot);
+        }
       }
+      if (ok) ok = push(0, 0, 0, META_END, 0);
       // wait for the last copies this warp issued (one per buffer) before the CTA can exit
       const long long n = it;
       for (long long k = (n > NBUF ? n - NBUF : 0); k < n; ++k) {
@@ -390,20 +409,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16(2 * CP);
-      long long it = 0, gstage = 0, run_start = w0;
-      int seg = 0;
+      long long it = 0, gstage = 0;
+      int seg = 0, run_pos = 0;
       bool ok = true;
-      for (long long w = w0; w < w1 && ok; ++w, ++it) {
+      for (;; ++it) {
         const int buf = (int)(it % NBUF);
-        const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
-        const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
-        if (first_in_run) run_start = w;
-        const bool seg_first = first_in_run || ((w - run_start) % F == 0);
-        const bool seg_last = last_in_run || ((w - run_start + 1) % F == 0);
         if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2)) {
           ok = false;
           break;
         }
+        const int flags = sMeta[buf].flags;
+        if (flags & META_END) break;
+        if (flags & META_FIRST) run_pos = 0;
+        const bool seg_first = (flags & META_FIRST) || (run_pos % F == 0);
+        const bool seg_last = (flags & META_LAST) || ((run_pos + 1) % F == 0);
+        ++run_pos;
         if (seg_first && seg > 0) {
           if (!mbar_wait(smem_u32(aempty), (uint32_t)(seg - 1) & 1u, abort_flag, p.err, 3)) {
             ok = false;
@@ -414,8 +434,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         const uint32_t sbuf = smem_u32(sB + buf * SM::B_BYTES);
         for (int st = 0; st < 2; ++st, ++gstage) {
           const int slot = (int)(gstage % SM::NSLOT);
-          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / SM::NSLOT) & 1u, abort_flag, p.err,
-                         4)) {
+          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / SM::NSLOT) & 1u, abort_flag,
+                         p.err, 4)) {
             ok = false;
             break;
           }
@@ -451,6 +471,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           ++seg;
         }
       }
+      (void)ok;
       // drain every MMA issued before the accumulators / TMEM go away
       tc_commit(smem_u32(drain));
       long long t0 = clock64();
@@ -492,17 +513,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         pending = -1;
       }
     };
-    long long it = 0, gstage = 0, run_start = w0;
-    int seg = 0, run = 0;
+    long long it = 0, gstage = 0;
+    int seg = 0, run = 0, run_pos = 0;
     bool ok = true;
-    long long cur_o = -1;
-    long long row_g = 0;
+    int cur_b = -1, cur_o = -1;
 #pragma unroll
     for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
     // A segment's accumulators are drained after the next stage has been generated, so
     // the generators never wait for the tensor core at segment ends.
     bool drain_due = false, d_out = false;
-    long long d_o = 0, d_row = 0;
+    int d_b = 0, d_slot = 0;
+    long long d_row = 0;
     // Add the segment accumulators to the running sums; at the end of a run also write
     // the run's output and clear the running sums.
     auto drain = [&]() -> bool {
@@ -528,21 +549,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       ++seg;
       if (!d_out) return true;
       // ---------------------------------------------------------------- run output
-      const long long slot_o = i - p.first_cta[d_o];
+      const InstDesc& d = desc(d_b);
       if (MODE == ENC) {
-        float2* dst = p.out + (slot_o * p.rows_total + d_row) * CP + cbase;
+        float2* dst = d.out + ((long long)d_slot * d.rows_total + d_row) * CP + cbase;
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-          const float sc = p.bscale[cbase + c];
+          const float sc = d.bscale[cbase + c];
           const float2 a = racc[c * NGT];
           dst[c] = make_float2(a.x * sc, a.y * sc);
         }
       } else {
-        const float2* Srow = p.S + d_row * CP + cbase;
+        const float2* Srow = d.S + d_row * CP + cbase;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-          const float sc = p.bscale[cbase + c];
+          const float sc = d.bscale[cbase + c];
           const float2 a = racc[c * NGT];
           const float xr = a.x * sc, xi = a.y * sc;
           const float2 sv = Srow[c];
@@ -564,7 +585,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
             v.x += sRed[k * 128 + row].x;
             v.y += sRed[k * 128 + row].y;
           }
-          p.out[slot_o * p.rows_total + d_row] = v;
+          d.out[(long long)d_slot * d.rows_total + d_row] = v;
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(edone));
         }
@@ -574,22 +595,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       ++run;
       return true;
     };
-    for (long long w = w0; w < w1 && ok; ++w, ++it) {
-      const int o = (int)(w / p.n_inner);
+    for (;; ++it) {
       const int buf = (int)(it % NBUF);
-      const bool first_in_run = (w == w0) || (w % p.n_inner == 0);
-      const bool last_in_run = (w + 1 == w1) || ((w + 1) % p.n_inner == 0);
-      if (first_in_run) run_start = w;
-      const bool seg_last = last_in_run || ((w - run_start + 1) % F == 0);
-      if (o != cur_o) {
-        cur_o = o;
-        row_g = (long long)o * 128 + row;
-#pragma unroll
-        for (int q = 0; q < RT; ++q) own[q] = p.rowT[((long long)o * RT + q) * 128 + row];
-      }
       if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5)) {
         ok = false;
         break;
+      }
+      const Meta m = sMeta[buf];
+      if (m.flags & META_END) break;
+      if (m.flags & META_FIRST) run_pos = 0;
+      const bool seg_last = (m.flags & META_LAST) || ((run_pos + 1) % F == 0);
+      ++run_pos;
+      if (m.o != cur_o || m.inst != cur_b) {
+        cur_o = m.o;
+        cur_b = m.inst;
+        const float* rT = desc(cur_b).rowT;
+#pragma unroll
+        for (int q = 0; q < RT; ++q) own[q] = rT[((long long)cur_o * RT + q) * 128 + row];
       }
       const float* col = sCol + buf * 128 * RT;
       const float* anc = sAnc + buf * 128;
@@ -598,8 +620,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       for (int st = 0; st < 2; ++st, ++gstage) {
         const int slot = (int)(gstage % SM::NSLOT);
         if (gstage >= SM::NSLOT &&
-            !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / SM::NSLOT - 1) & 1u, abort_flag,
-                       p.err, 6)) {
+            !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / SM::NSLOT - 1) & 1u,
+                       abort_flag, p.err, 6)) {
           ok = false;
           break;
         }
@@ -623,11 +645,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
             t[3] = __fadd2_rn(make_float2(a8.z, a8.w), rb2);
 #pragma unroll
             for (int q = 0; q < RT; ++q) {
-              const float4 d = *reinterpret_cast<const float4*>(col + q * 128 + v0);
+              const float4 dd = *reinterpret_cast<const float4*>(col + q * 128 + v0);
               const float4 e = *reinterpret_cast<const float4*>(col + q * 128 + v0 + 4);
               const float2 o2 = make_float2(own[q], own[q]);
-              t[0] = __ffma2_rn(o2, make_float2(d.x, d.y), t[0]);
-              t[1] = __ffma2_rn(o2, make_float2(d.z, d.w), t[1]);
+              t[0] = __ffma2_rn(o2, make_float2(dd.x, dd.y), t[0]);
+              t[1] = __ffma2_rn(o2, make_float2(dd.z, dd.w), t[1]);
               t[2] = __ffma2_rn(o2, make_float2(e.x, e.y), t[2]);
               t[3] = __ffma2_rn(o2, make_float2(e.z, e.w), t[3]);
             }
@@ -680,9 +702,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       if (seg_last) {
         // drain after the next stage has been generated (or at the end)
         drain_due = true;
-        d_out = last_in_run;
-        d_o = o;
-        d_row = row_g;
+        d_out = (m.flags & META_LAST) != 0;
+        d_b = m.inst;
+        d_slot = m.slot;
+        d_row = (long long)m.o * 128 + row;
       }
     }
     if (ok && drain_due) {
@@ -707,7 +730,7 @@ template <int CP, int RP, int NPART>
 constexpr size_t smem_bytes() {
   constexpr int NB = Smem<CP, NPART>::NBUFS;
   return 1024 + NB * Smem<CP, NPART>::B_BYTES + NB * 128 * RP * 4 + 2 * NB * 128 * 4 +
-         4 * 128 * 8 + (CP / 4) * NGEN_WARPS * 32 * 8 + 24 * 8 + 16;
+         4 * 128 * 8 + (CP / 4) * NGEN_WARPS * 32 * 8 + NB * sizeof(Meta) + 24 * 8 + 16;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -835,26 +858,38 @@ static int launch_pass(sense_plan_s* P, const tc::Params& prm, int G, cudaStream
 }
 
 template <int MODE, int CP, int NPART>
-static int dispatch_rp(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
-  switch (P->RT) {
+static int dispatch_rp(sense_plan_s* P, int rt, const tc::Params& prm, int G, cudaStream_t st) {
+  switch (rt) {
     case 4: return launch_pass<MODE, CP, 4, NPART>(P, prm, G, st);
     case 6: return launch_pass<MODE, CP, 6, NPART>(P, prm, G, st);
     case 8: return launch_pass<MODE, CP, 8, NPART>(P, prm, G, st);
     case 10: return launch_pass<MODE, CP, 10, NPART>(P, prm, G, st);
     case 12: return launch_pass<MODE, CP, 12, NPART>(P, prm, G, st);
     case 16: return launch_pass<MODE, CP, 16, NPART>(P, prm, G, st);
-    default: return launch_pass<MODE, CP, 20, NPART>(P, prm, G, st);
+    case 20: return launch_pass<MODE, CP, 20, NPART>(P, prm, G, st);
+    default: return set_error(SENSE_EUNSUPPORTED, "delta rows not in {4,6,8,10,12,16,20}");
   }
 }
 
 template <int MODE, int NPART>
-static int dispatch_cp(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
-  switch (P->Cp) {
-    case 8: return dispatch_rp<MODE, 8, NPART>(P, prm, G, st);
-    case 16: return dispatch_rp<MODE, 16, NPART>(P, prm, G, st);
-    case 32: return dispatch_rp<MODE, 32, NPART>(P, prm, G, st);
-    default: return dispatch_rp<MODE, 64, NPART>(P, prm, G, st);
+static int dispatch_cp(sense_plan_s* P, int cp, int rt, const tc::Params& prm, int G,
+                       cudaStream_t st) {
+  switch (cp) {
+    case 8: return dispatch_rp<MODE, 8, NPART>(P, rt, prm, G, st);
+    case 16: return dispatch_rp<MODE, 16, NPART>(P, rt, prm, G, st);
+    case 32: return dispatch_rp<MODE, 32, NPART>(P, rt, prm, G, st);
+    case 64: return dispatch_rp<MODE, 64, NPART>(P, rt, prm, G, st);
+    default: return set_error(SENSE_EUNSUPPORTED, "padded coils not in {8,16,32,64}");
   }
+}
+
+int tc_launch(sense_plan_s* P, int mode, int npart, int cp, int rt, const tc::Params& prm, int G,
+              cudaStream_t st) {
+  if (mode == tc::ENC)
+    return npart == 2 ? dispatch_cp<tc::ENC, 2>(P, cp, rt, prm, G, st)
+                      : dispatch_cp<tc::ENC, 1>(P, cp, rt, prm, G, st);
+  return npart == 2 ? dispatch_cp<tc::ADJ, 2>(P, cp, rt, prm, G, st)
+                    : dispatch_cp<tc::ADJ, 1>(P, cp, rt, prm, G, st);
 }
 
 static void tc_free_layout(sense_plan_s* P) {
@@ -992,9 +1027,27 @@ static int vgrid(sense_plan_s* P, long long n) {
   return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8 * P->num_sms));
 }
 
-static int make_image(sense_plan_s* P, int npart, const float2* src, const float2* pv,
-                      long long nrows, unsigned* colmax, float* bscale, uint8_t* img,
-                      bool have_colmax, cudaStream_t st) {
+int tc_reduce_y(sense_plan_s* P, const float2* Ypart, const int* nslot, float2* Y_int,
+                float2* s_user, unsigned* cm, const double* stop, cudaStream_t st) {
+  if (cm) SENSE_CUDA_TRY(cudaMemsetAsync(cm, 0, P->Cp * 4, st));
+  tc_reduce_y_kernel<<<vgrid(P, P->Kp * P->Cp), 256, 0, st>>>(Ypart, nslot, P->K, P->Kp, P->C,
+                                                              P->Cp, Y_int, s_user, cm, stop);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  return SENSE_OK;
+}
+
+int tc_reduce_x(sense_plan_s* P, const float2* Xpart, const int* nslot, float2* q,
+                const double* stop, cudaStream_t st) {
+  tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(Xpart, nslot, P->Lp, q, stop);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  count_launch(P);
+  return SENSE_OK;
+}
+
+int tc_make_image(sense_plan_s* P, int npart, const float2* src, const float2* pv,
+                  long long nrows, unsigned* colmax, float* bscale, uint8_t* img,
+                  bool have_colmax, cudaStream_t st) {
   if (!have_colmax) {
     SENSE_CUDA_TRY(cudaMemsetAsync(colmax, 0, P->Cp * 4, st));
     tc::colmax_kernel<<<vgrid(P, nrows * P->Cp), 256, 0, st>>>(src, P->S, pv, nrows, P->Cp, colmax);
@@ -1015,29 +1068,31 @@ static int make_image(sense_plan_s* P, int npart, const float2* src, const float
 
 static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, const float* bscale,
                     float2* out, const double* stop, cudaStream_t st) {
-  tc::Params prm;
+  tc::Params prm = {};
   const bool enc = mode == tc::ENC;
-  prm.rowT = enc ? P->dKt : P->dRt;
-  prm.colT = enc ? P->dRt : P->dKt;
-  prm.rowAnc = enc ? P->Banc : P->Aanc;
-  prm.colAnc = enc ? P->Aanc : P->Banc;
-  prm.Bimg = img;
-  prm.bscale = bscale;
-  prm.S = P->S;
-  prm.out = out;
+  tc::InstDesc& d = prm.d0;
+  d.rowT = enc ? P->dKt : P->dRt;
+  d.colT = enc ? P->dRt : P->dKt;
+  d.rowAnc = enc ? P->Banc : P->Aanc;
+  d.colAnc = enc ? P->Aanc : P->Banc;
+  d.Bimg = img;
+  d.bscale = bscale;
+  d.S = P->S;
+  d.out = out;
+  d.stop = nullptr;
+  d.rows_total = enc ? P->Kp : P->Lp;
+  d.cols_total = enc ? P->Lp : P->Kp;
+  d.n_outer = enc ? P->nsb : P->nvb;
+  d.n_inner = enc ? P->nvb : P->nsb;
+  d.chunk = d.n_inner;
+  prm.inst = nullptr;
   prm.first_cta = enc ? P->tc_first_e : P->tc_first_a;
+  prm.W = (long long)d.n_outer * d.n_inner;
   prm.err = P->tc_err;
   prm.stop = stop;
-  prm.rows_total = enc ? P->Kp : P->Lp;
-  prm.cols_total = enc ? P->Lp : P->Kp;
-  prm.n_outer = enc ? P->nsb : P->nvb;
-  prm.n_inner = enc ? P->nvb : P->nsb;
-  prm.W = (long long)prm.n_outer * prm.n_inner;
   prm.seg_len = P->tc_seg_len;
   const int G = P->tc_grid;
-  if (enc)
-    return npart == 2 ? dispatch_cp<tc::ENC, 2>(P, prm, G, st) : dispatch_cp<tc::ENC, 1>(P, prm, G, st);
-  return npart == 2 ? dispatch_cp<tc::ADJ, 2>(P, prm, G, st) : dispatch_cp<tc::ADJ, 1>(P, prm, G, st);
+  return tc_launch(P, mode, npart, P->Cp, P->RT, prm, G, st);
 }
 
 static int npart_of(int prec) { return prec == SENSE_PREC_TC_SPLIT ? 2 : 1; }
@@ -1047,16 +1102,11 @@ int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, fl
               bool want_colmax, const double* stop, cudaStream_t st) {
   const int np = npart_of(prec);
   int rc;
-  if ((rc = make_image(P, np, nullptr, p_plan, P->Lp, P->colmax, P->qscale, P->Qimg, false, st)))
+  if ((rc = tc_make_image(P, np, nullptr, p_plan, P->Lp, P->colmax, P->qscale, P->Qimg, false, st)))
     return rc;
   if ((rc = run_pass(P, tc::ENC, np, P->Qimg, P->qscale, P->Ypart_tc, stop, st))) return rc;
   unsigned* cm = want_colmax ? P->colmax + P->Cp : nullptr;
-  if (cm) SENSE_CUDA_TRY(cudaMemsetAsync(cm, 0, P->Cp * 4, st));
-  tc_reduce_y_kernel<<<vgrid(P, P->Kp * P->Cp), 256, 0, st>>>(
-      P->Ypart_tc, P->tc_nslot_e, P->K, P->Kp, P->C, P->Cp, Y_int, s_user, cm, stop);
-  SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
-  return SENSE_OK;
+  return tc_reduce_y(P, P->Ypart_tc, P->tc_nslot_e, Y_int, s_user, cm, stop, st);
 }
 
 // q <- E^H Y_int (plan order). colmax_ready: P->colmax + Cp already holds Y's maxima.
@@ -1064,14 +1114,11 @@ int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool c
                const double* stop, cudaStream_t st) {
   const int np = npart_of(prec);
   int rc;
-  if ((rc = make_image(P, np, Y_int, nullptr, P->Kp, P->colmax + P->Cp, P->yscale, P->Yimg,
+  if ((rc = tc_make_image(P, np, Y_int, nullptr, P->Kp, P->colmax + P->Cp, P->yscale, P->Yimg,
                        colmax_ready, st)))
     return rc;
   if ((rc = run_pass(P, tc::ADJ, np, P->Yimg, P->yscale, P->Xpart_tc, stop, st))) return rc;
-  tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(P->Xpart_tc, P->tc_nslot_a, P->Lp, q, stop);
-  SENSE_CUDA_TRY(cudaGetLastError());
-  count_launch(P);
-  return SENSE_OK;
+  return tc_reduce_x(P, P->Xpart_tc, P->tc_nslot_a, q, stop, st);
 }
 
 int tc_check_error(sense_plan_s* P) {

@@ -1,0 +1,71 @@
+// Tensor-core pass: the data the pass kernel reads and the host entry points shared by the
+// single-problem operator (sense_tc.cu) and the batched solver (sense_batch.cu).
+#pragma once
+#include "sense_internal.cuh"
+
+namespace sense {
+namespace tc {
+
+// One problem instance as the pass kernel sees it.
+struct InstDesc {
+  const float* rowT;     // [n_outer][RT][128] own-dimension deltas (dK for ENC, dR for ADJ)
+  const float* colT;     // [n_inner][RT][128] streamed deltas
+  const float* rowAnc;   // [n_inner][rows_total] (Banc for ENC, Aanc for ADJ)
+  const float* colAnc;   // [n_outer][cols_total] (Aanc for ENC, Banc for ADJ)
+  const uint8_t* Bimg;   // [n_inner][2 halves][NPART][2*CP rows][128 B]
+  const float* bscale;   // [CP] 2^-e unscale per coil
+  const float2* S;       // [rows_total][CP] (ADJ epilogue)
+  float2* out;           // ENC: [slots][rows_total][CP]; ADJ: [slots][rows_total]
+  const double* stop;    // CG stop flag of the instance (nullable; work queue only)
+  long long rows_total, cols_total;
+  int n_outer, n_inner;
+  int chunk;             // work queue: streamed blocks per work item (slot = first / chunk)
+  int pad;
+};
+
+// Two schedules feed the same kernel:
+//   stream-K (one instance, inst == nullptr): CTA i takes the pairs [iW/G, (i+1)W/G) of the
+//     flattened (row block, streamed block) space; a row block's partial slot is
+//     i - first_cta[row block];
+//   work queue (inst != nullptr): CTAs claim items {instance, row block, first, end streamed
+//     block} with an atomic counter (zeroed before the launch), skipping stopped instances;
+//     an item is one run and its slot is first / chunk.
+struct Params {
+  InstDesc d0;           // the instance of the stream-K schedule
+  const InstDesc* inst;  // work queue: per-instance descriptors
+  const int4* items;     // work queue: [n_items]
+  unsigned* next;        // work queue: claim counter
+  int n_items;
+  const int* first_cta;  // stream-K: [n_outer]
+  long long W;           // stream-K: n_outer * n_inner
+  int* err;              // device error word (nonzero after a time-out)
+  const double* stop;    // stream-K: CG stop flag (nullable)
+  int seg_len;           // accumulator drain interval (pairs of 128 x 128)
+};
+
+// Per-stage metadata passed from the loader to the MMA and generator warps.
+struct Meta {
+  int inst, o, in, flags;  // flags: bit 0 first pair of a run, bit 1 last pair, bit 2 end
+  int slot, pad0, pad1, pad2;
+};
+constexpr int META_FIRST = 1, META_LAST = 2, META_END = 4;
+
+enum Mode { ENC = 0, ADJ = 1 };
+
+}  // namespace tc
+
+// Launch one pass (template chosen by npart, cp = padded coils, rt = delta rows) on G CTAs.
+int tc_launch(sense_plan_s* P, int mode, int npart, int cp, int rt, const tc::Params& prm, int G,
+              cudaStream_t st);
+// B image of src (Y_int layout, nrows x Cp) or of S o pv; colmax computed unless have_colmax.
+int tc_make_image(sense_plan_s* P, int npart, const float2* src, const float2* pv,
+                  long long nrows, unsigned* colmax, float* bscale, uint8_t* img,
+                  bool have_colmax, cudaStream_t st);
+// Sum of partial slots: Y_int / s_user (+ colmax) from Ypart [slots][Kp][Cp] with nslot per
+// sample block; q from Xpart [slots][Lp] with nslot per voxel block.
+int tc_reduce_y(sense_plan_s* P, const float2* Ypart, const int* nslot, float2* Y_int,
+                float2* s_user, unsigned* colmax, const double* stop, cudaStream_t st);
+int tc_reduce_x(sense_plan_s* P, const float2* Xpart, const int* nslot, float2* q,
+                const double* stop, cudaStream_t st);
+
+}  // namespace sense

@@ -29,7 +29,10 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_lcurve_corner", "sense_strerror", "sense_last_error", "sense_plan_profile",
             "sense_plan_stats", "sense_diag_sincos_rate", "sense_plan_get_tuning",
             "sense_plan_set_tuning", "sense_plan_sync", "sense_encode_noalloc",
-            "sense_grad_b0", "sense_cg_ckpt_bytes", "sense_cg_solve_ckpt", "sense_cg_backward"]
+            "sense_grad_b0", "sense_cg_ckpt_bytes", "sense_cg_solve_ckpt", "sense_cg_backward",
+            "sense_batch_create", "sense_batch_destroy", "sense_batch_plan", "sense_batch_info",
+            "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
+            "sense_batch_autotune"]
 
 
 class SenseError(RuntimeError):
@@ -94,6 +97,16 @@ def _load():
         "sense_cg_solve_ckpt": ([vp, vp, vp, ctypes.POINTER(CGOpts), i32, vp, i64,
                                  ctypes.POINTER(CGInfo), vp], ctypes.c_int),
         "sense_cg_backward": ([vp, vp, vp, i64, vp, vp, vp, vp], ctypes.c_int),
+        "sense_batch_create": ([ctypes.POINTER(_Problem), i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "sense_batch_destroy": ([vp], ctypes.c_int),
+        "sense_batch_plan": ([vp, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "sense_batch_info": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
+        "sense_batch_normal_op": ([vp, i32, vp, vp, vp], ctypes.c_int),
+        "sense_batch_cg_solve": ([vp, vp, vp, ctypes.POINTER(CGOpts), ctypes.POINTER(CGInfo), vp],
+                                 ctypes.c_int),
+        "sense_batch_set_tuning": ([vp, i32, i32], ctypes.c_int),
+        "sense_batch_autotune": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                  ctypes.POINTER(dbl)], ctypes.c_int),
         "sense_plan_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
@@ -277,6 +290,123 @@ def sense_cg_backward(plan, s, ckpt, xbar, sbar=None, omega_bar=None, stream=Non
     pwb, _, _ = _ptr(omega_bar, np.float32)
     _check(_lib.sense_cg_backward(plan, ps, pc, int(kc.numel()), pxb, psb, pwb,
                                   _stream(ss, sxb, explicit=stream)), "sense_cg_backward")
+
+
+def _problem_struct(Kmat, Rmat, S, j, keep):
+    Kmat = np.ascontiguousarray(Kmat, np.float64)
+    Rmat = np.ascontiguousarray(Rmat, np.float64)
+    S = np.ascontiguousarray(S, np.complex64)
+    jj = None if j is None else np.ascontiguousarray(j, np.float32)
+    K, P1 = Kmat.shape
+    L = Rmat.shape[1]
+    if Rmat.shape[0] != P1 or S.shape[0] != L or (jj is not None and jj.shape != (L,)):
+        raise ValueError("inconsistent shapes")
+    keep.extend([Kmat, Rmat, S, jj])
+    return _Problem(L, K, S.shape[1], P1, Kmat.ctypes.data, Rmat.ctypes.data, S.ctypes.data,
+                    None if jj is None else jj.ctypes.data)
+
+
+def sense_batch_create(problems):
+    """problems: sequence of (Kmat, Rmat, S, j). Returns an opaque batch handle (int)."""
+    keep = []
+    arr = (_Problem * len(problems))(*[_problem_struct(*p, keep) for p in problems])
+    h = ctypes.c_void_p()
+    _check(_lib.sense_batch_create(arr, len(problems), ctypes.byref(h)), "sense_batch_create")
+    return h.value
+
+
+def sense_batch_destroy(batch):
+    _check(_lib.sense_batch_destroy(batch), "sense_batch_destroy")
+
+
+def sense_batch_plan(batch, i):
+    h = ctypes.c_void_p()
+    _check(_lib.sense_batch_plan(batch, int(i), ctypes.byref(h)), "sense_batch_plan")
+    return h.value
+
+
+def sense_batch_info(batch):
+    out = (ctypes.c_int32 * 4)()
+    _check(_lib.sense_batch_info(batch, out), "sense_batch_info")
+    return dict(zip(["n", "C_padded", "delta_rows", "chunk"], list(out)))
+
+
+def _ptr_array(tensors):
+    ptrs = [_ptr(t)[0] for t in tensors]
+    return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+
+def sense_batch_normal_op(batch, prec, m_list, out_list, stream=None):
+    """out_list[b] = E_b^H E_b m_list[b] (complex64 CUDA tensors)."""
+    st = stream if stream is not None else _ptr(m_list[0])[2]
+    _check(_lib.sense_batch_normal_op(batch, int(prec), _ptr_array(m_list), _ptr_array(out_list),
+                                      st), "sense_batch_normal_op")
+
+
+def sense_batch_cg_solve(batch, s_list, x_list, max_iter, prec=SENSE_PREC_TC_SPLIT, rel_tol=0.0,
+                         apply_j=True, stream=None):
+    """CG for every instance (device tensors); returns the list of info dicts."""
+    n = len(s_list)
+    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), 0, 1 if apply_j else 0)
+    infos = (CGInfo * n)()
+    st = stream if stream is not None else _ptr(s_list[0])[2]
+    _check(_lib.sense_batch_cg_solve(batch, _ptr_array(s_list), _ptr_array(x_list),
+                                     ctypes.byref(opts), infos, st), "sense_batch_cg_solve")
+    return [dict(iters=i.iters, status=i.status, rr0=i.rr0, rr_final=i.rr_final) for i in infos]
+
+
+def sense_batch_set_tuning(batch, chunk=16, seg_len=4):
+    _check(_lib.sense_batch_set_tuning(batch, int(chunk), int(seg_len)), "sense_batch_set_tuning")
+
+
+def sense_batch_autotune(batch, prec=SENSE_PREC_TC_SPLIT):
+    c, s, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(_lib.sense_batch_autotune(batch, int(prec), ctypes.byref(c), ctypes.byref(s),
+                                     ctypes.byref(ms)), "sense_batch_autotune")
+    return {"chunk": c.value, "seg_len": s.value, "ms": ms.value}
+
+
+class Batch:
+    """Owns a libsense batch of independent problems (sequence of (Kmat, Rmat, S, j))."""
+
+    def __init__(self, problems):
+        self.handle = sense_batch_create(problems)
+        self.n = len(problems)
+        self.dims = []
+        for i in range(self.n):
+            inf = sense_plan_info(sense_batch_plan(self.handle, i))
+            self.dims.append((inf["L"], inf["K"], inf["C"]))
+
+    def close(self):
+        if self.handle:
+            sense_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def normal(self, ms, prec=SENSE_PREC_TC_SPLIT):
+        import torch
+        outs = [torch.empty_like(m) for m in ms]
+        sense_batch_normal_op(self.handle, prec, ms, outs)
+        torch.cuda.synchronize()
+        return outs
+
+    def cg(self, ss, max_iter, prec=SENSE_PREC_TC_SPLIT, rel_tol=0.0, apply_j=True):
+        import torch
+        xs = [torch.empty(L, dtype=torch.complex64, device=s.device)
+              for s, (L, _, _) in zip(ss, self.dims)]
+        infos = sense_batch_cg_solve(self.handle, ss, xs, max_iter, prec, rel_tol, apply_j)
+        return xs, infos
 
 
 def sense_plan_sync(plan, stream=None):

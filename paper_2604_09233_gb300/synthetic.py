@@ -263,6 +263,35 @@ def target_256():
                           4, 150.0, order=3, n_iter=40)
 
 
+def batch_64(n=64, seed=5000):
+    """64 independent 2D spiral instances of uneven size: matrix uniform in
+    {64,96,128,192,256}^2, coils in {8,16,32}, 4096-35750 samples at 2 us, R in {2,3,4},
+    B0 +-50..150 Hz, field expansion of order 1..3; 50 CG iterations at most, stop at a
+    relative residual of 1e-3. Instance i uses seed + i; the sizes are drawn with seed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        matrix = int(rng.choice([64, 96, 128, 192, 256]))
+        coils = int(rng.choice([8, 16, 32]))
+        samples = int(rng.integers(4096, 35751))
+        R = int(rng.choice([2, 3, 4]))
+        order = int(rng.integers(1, 4))
+        fmax = float(rng.uniform(50.0, 150.0))
+        out.append(make_spiral_2d(f"b{i}_{matrix}x{matrix}_{coils}c_{samples}s_o{order}",
+                                  seed + i, matrix, 0.22, coils, samples, 2e-6, R, fmax,
+                                  order=order, n_iter=50))
+    return out
+
+
+def small_batch(seed=7000):
+    """Five small instances of uneven size for batch parity tests (ragged tiles, 1..32 coils,
+    orders 1..3, one with intensity correction j)."""
+    spec = [(24, 8, 1500, 3, True), (12, 3, 300, 1, False), (20, 32, 1000, 2, False),
+            (8, 1, 100, 1, False), (16, 16, 600, 3, False)]
+    return [small_2d(seed=seed + i, matrix=mtx, n_coils=c, n_samples=k, order=o, with_j=wj)
+            for i, (mtx, c, k, o, wj) in enumerate(spec)]
+
+
 def small_2d(seed=7, matrix=24, n_coils=8, n_samples=1500, order=3, R=2, f_max_hz=80.0,
              with_j=False, dwell=4e-6, n_iter=10):
     """Small problem of the same family for parity tests (oracle runs in well under a second)."""
