@@ -41,7 +41,7 @@ def _parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tc_fp16", "tc_split"])
     ap.add_argument("--workload", default="target_256",
-                    choices=["target_256", "precision_128", "plain_32", "batch_64"])
+                    choices=["target_256", "precision_128", "plain_32", "stack_3d", "batch_64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--op-only", action="store_true",
                     help="time only W + K single E^H E applies (used for kernel profiling)")

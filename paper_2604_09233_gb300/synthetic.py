@@ -238,6 +238,60 @@ def make_spiral_2d(name, seed, matrix, fov, n_coils, n_samples, dwell, R, f_max_
                     shape, n_iter, meta)
 
 
+def make_stack_of_spirals_3d(name, seed, shape, fov, fov_z, n_coils, n_arm_samples, dwell,
+                             R_z, arms, R_arm, f_max_hz, order=2, ho_scale=1e-3,
+                             noise_sigma=1e-3, n_iter=30):
+    """3D stack of spirals. Every R_z-th of the nz kz planes is acquired; each plane carries
+    `arms` spiral-out arms (each R_arm-fold undersampled, rotated by 2 pi / arms, the set
+    turned by a further golden-angle step from plane to plane), so R = R_z R_arm / arms.
+    Every arm is one readout: t restarts at 0. Linear terms are (kx, ky, kz); the other
+    solid-harmonic terms up to `order` are smooth random cubic splines of t (shared by all
+    arms) at ho_scale of the linear amplitude."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nz, ny, nx = shape
+    x, y, z = grid_positions(shape, (fov, fov, fov_z))
+    L = x.shape[0]
+    kx0, ky0 = spiral_2d(n_arm_samples, nx, fov, R_arm)
+    t_arm = np.arange(n_arm_samples) * dwell
+    planes = np.arange(-(nz // 2), nz - nz // 2, R_z)
+    golden = np.pi * (3.0 - np.sqrt(5.0))
+    kx, ky, kz, t = [], [], [], []
+    for ip, u in enumerate(planes):
+        for a in range(arms):
+            th = 2 * np.pi * a / arms + golden * ip
+            kx.append(kx0 * np.cos(th) - ky0 * np.sin(th))
+            ky.append(kx0 * np.sin(th) + ky0 * np.cos(th))
+            kz.append(np.full(n_arm_samples, 2 * np.pi * u / fov_z))
+            t.append(t_arm)
+    kx, ky, kz, t = (np.concatenate(v) for v in (kx, ky, kz, t))
+    K = t.shape[0]
+    omega = b0_map(rng, x, y, fov, f_max_hz, z=z, fov_z=fov_z)
+    h = field_basis_rows(x, y, z, order)
+    kt = np.zeros((K, h.shape[0]))
+    kt[:, 1], kt[:, 2], kt[:, 3] = kx, ky, kz
+    r_max = np.max(np.sqrt(x * x + y * y + z * z))
+    lin_max = np.max(np.sqrt(kx * kx + ky * ky + kz * kz)) * r_max
+    for p in range(h.shape[0]):
+        if SH_TERMS[p][0] == 1:
+            continue
+        spl = _cubic_spline_coeffs(rng, t_arm)
+        hmax = np.max(np.abs(h[p])) or 1.0
+        kt[:, p] = np.tile(ho_scale * lin_max * spl / (np.max(np.abs(spl)) * hmax),
+                           K // n_arm_samples)
+    Rm = np.vstack([omega[None, :], h])
+    Km = np.hstack([t[:, None], kt])
+    zr = [(-1.5 + k) * fov_z / 2 for k in range(4)]
+    S = coils(rng, x, y, z, n_coils, fov, z_rings=zr)
+    m = phantom(rng, x, y, fov, z=z, fov_z=fov_z)
+    noise = _c64((rng.normal(size=(K, n_coils)) + 1j * rng.normal(size=(K, n_coils)))
+                 * noise_sigma / np.sqrt(2.0))
+    meta = dict(fov=fov, fov_z=fov_z, dwell=dwell, R=R_z * R_arm / arms, f_max_hz=f_max_hz,
+                order=order, seed=seed, planes=len(planes), arms=arms,
+                T_acq_ms=n_arm_samples * dwell * 1e3)
+    return Workload(name, np.ascontiguousarray(Km), np.ascontiguousarray(Rm), S, m, noise, None,
+                    shape, n_iter, meta)
+
+
 # ---------------------------------------------------------------------------------------
 # Named workloads. Seeds follow seed = 1000 * config + instance.
 # ---------------------------------------------------------------------------------------
@@ -261,6 +315,24 @@ def target_256():
     3rd-order solid harmonics, 40 CG iterations."""
     return make_spiral_2d("2d_256x256_32coil_35750samp_sh3", 3000, 256, 0.22, 32, 35750, 2e-6,
                           4, 150.0, order=3, n_iter=40)
+
+
+def stack_3d():
+    """3D 96x96x48 (442368 voxels), FOV 220 x 220 x 96 mm, 32 coils on 4 rings; stack of
+    spirals with 16 of 48 kz planes x 3 arms of 1300 samples at 2 us (62400 samples, R = 7);
+    B0 3D polynomial plus blobs, +-200 Hz; 2nd-order solid harmonics (9 terms); 30 CG
+    iterations."""
+    return make_stack_of_spirals_3d("3d_96x96x48_32coil_62400samp_sh2", 4000, (48, 96, 96),
+                                    0.22, 0.096, 32, 1300, 2e-6, 3, 3, 7, 200.0, order=2,
+                                    n_iter=30)
+
+
+def small_3d(seed=4100, shape=(8, 16, 16), n_coils=8, n_arm_samples=200, R_z=2, arms=2,
+             R_arm=2, order=2):
+    """Small stack of spirals of the same family for parity tests."""
+    return make_stack_of_spirals_3d(f"small3d_{'x'.join(map(str, shape))}_{n_coils}c", seed,
+                                    shape, 0.22, 0.096, n_coils, n_arm_samples, 4e-6, R_z, arms,
+                                    R_arm, 100.0, order=order, n_iter=10)
 
 
 def batch_64(n=64, seed=5000):
