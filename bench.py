@@ -245,6 +245,31 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
+# DRAM bytes per launch of the tensor-core passes (dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture, profiles/tc_pass_2d256_32coil_sh3.md), keyed by the SHA-256 of the
+# kernel sources they were taken on; any other source reports null.
+KERNEL_TRAFFIC = {
+    "bea06ac62cbf0822d01d6f3678d65ab68fdfe877381e1f01a4e8b94435ede104": {
+        "workload": "2d_256x256_32coil_35750samp_sh3", "precision": "tc_split",
+        "tc_encode_pass": (169.044736 + 9.572608) * 1e6,
+        "tc_adjoint_pass": (182.273280 + 3.996928) * 1e6,
+    },
+}
+
+
+def _kernel_traffic(workload, prec_name, kernel):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2604_09233_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("sense_tc.cu", "sense_tc.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    rec = KERNEL_TRAFFIC.get(h.hexdigest())
+    if not rec or rec["workload"] != workload or rec["precision"] != prec_name:
+        return None
+    return rec.get(kernel)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -362,12 +387,13 @@ def run_ours(args):
     flops = pairs * mma_per_pair * 2 * (2 * Cp)    # 2 * N per pair per MMA, N = 2 Cp
     tflops = flops / t_launch / 1e12
     peak_tc = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    traffic = _kernel_traffic(wl.name, prec_name, kc)
     sfu = {"bound": "alu", "achieved": achieved_sincos / 1e9, "peak": sincos_peak / 1e9,
-           "unit": "Gsincos/s", "frac": achieved_sincos / sincos_peak, "traffic": None,
+           "unit": "Gsincos/s", "frac": achieved_sincos / sincos_peak, "traffic": traffic,
            "kernel": kc, "per_launch_ms": t_launch * 1e3,
            "peak_source": "measured on this GPU by sense_diag_sincos_rate"}
     tensor = {"bound": "tensor", "achieved": tflops, "peak": peak_tc, "unit": "TFLOP/s",
-              "frac": tflops / peak_tc, "traffic": None, "kernel": kc,
+              "frac": tflops / peak_tc, "traffic": traffic, "kernel": kc,
               "peak_source": f"bf16 sustained, {peak_kind} (fp16 = bf16 rate)"}
     roof = sfu if sfu["frac"] >= tensor["frac"] else tensor
 
