@@ -270,6 +270,23 @@ def _kernel_traffic(workload, prec_name, kernel):
     return rec.get(kernel)
 
 
+def max_over_ranks(total_ms, world, device=None):
+    """The largest of the ranks' timed totals, returned on every rank (the job takes as long
+    as its slowest replica)."""
+    if world <= 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -330,12 +347,8 @@ def run_ours(args):
     native.sense_plan_profile(plan.handle, False)
     if world > 1:
         dist.barrier()
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_it * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(np.sum(times)), world, dev)
+    value = job_rate(n_it * args.steps, world, total_ms)
     x_tc = x.clone()
 
     # ---------------------------------------------------------------- comparisons (untimed)
@@ -369,7 +382,8 @@ def run_ours(args):
                               history=False)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * n_it * len(e2e_t) / float(np.sum(e2e_t))
+    e2e_value = job_rate(n_it * len(e2e_t), world,
+                         max_over_ranks(1e3 * float(np.sum(e2e_t)), world, dev))
 
     # ---------------------------------------------------------------- roofline
     # dominant kernel: the tensor-core pass (E or E^H) with the larger share of event time

@@ -90,3 +90,44 @@ def test_lcurve_corner_matches_oracle_picker():
     c_lib = native.sense_lcurve_corner(hist)
     c_or = oracle.lcurve_corner(res, sol)
     assert c_lib == c_or and 0 < c_lib < len(n) - 1
+
+
+def test_gradient_and_batch_entry_points_check_arguments_first():
+    """The differentiation, batch and allocation-free entry points reject null handles and
+    impossible sizes before any device work (so these checks need no GPU)."""
+    from paper_2604_09233_gb300 import native
+    lib = native._lib
+    vp = ctypes.c_void_p
+    assert lib.sense_grad_b0(None, 0, None, None, None, None, None) == -1
+    assert lib.sense_cg_ckpt_bytes(None, 10, 2) == -1
+    assert lib.sense_cg_solve_ckpt(None, None, None, None, 2, None, 0, None, None) == -1
+    assert lib.sense_cg_backward(None, None, None, 0, None, None, None, None) == -1
+    h = vp()
+    assert lib.sense_batch_create(None, 0, ctypes.byref(h)) == -1
+    assert lib.sense_batch_destroy(None) == 0
+    assert lib.sense_batch_plan(None, 0, ctypes.byref(h)) == -1
+    assert lib.sense_batch_info(None, (ctypes.c_int32 * 4)()) == -1
+    assert lib.sense_batch_normal_op(None, 2, None, None, None) == -1
+    assert lib.sense_batch_cg_solve(None, None, None, None, None, None) == -1
+    assert lib.sense_batch_set_tuning(None, 16, 4) == -1
+    assert lib.sense_batch_autotune(None, 2, None, None, None) == -1
+    d = ctypes.c_double()
+    buf = (ctypes.c_float * 8)()
+    # the allocation-free encode: sizes first (L < 1), then its fixed scratch (K x 32 coils
+    # one sample row beyond 2^21 complex values)
+    assert lib.sense_encode_noalloc(0, 4, 8, 1, ctypes.addressof(d), ctypes.addressof(d),
+                                    buf, None, buf, buf, None) == -1
+    assert lib.sense_encode_noalloc(4, (1 << 21) // 32 + 1, 32, 1, ctypes.addressof(d),
+                                    ctypes.addressof(d), buf, None, buf, buf, None) == -1
+    assert b"scratch" in lib.sense_last_error()
+
+
+def test_batch_create_without_gpu_reports_no_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2604_09233_gb300 import native
+    with pytest.raises(native.SenseError) as e:
+        native.sense_batch_create([(np.zeros((4, 1)), np.zeros((1, 5)),
+                                    np.zeros((5, 2), np.complex64), None)])
+    assert e.value.code == -7
