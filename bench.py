@@ -247,9 +247,9 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # DRAM bytes per launch of the tensor-core passes (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture, profiles/tc_pass_2d256_32coil_sh3.md), keyed by the SHA-256 of the
-# kernel sources they were taken on; any other source reports null.
+# pass-kernel source they were taken on (pass_kernel_source_hash); any other source reports null.
 KERNEL_TRAFFIC = {
-    "bea06ac62cbf0822d01d6f3678d65ab68fdfe877381e1f01a4e8b94435ede104": {
+    "cc41474d781cf7698599f881f02bc82b59d59ab57b6a57c98974a18e31b10b03": {
         "workload": "2d_256x256_32coil_35750samp_sh3", "precision": "tc_split",
         "tc_encode_pass": (169.044736 + 9.572608) * 1e6,
         "tc_adjoint_pass": (182.273280 + 3.996928) * 1e6,
@@ -257,14 +257,22 @@ KERNEL_TRAFFIC = {
 }
 
 
-def _kernel_traffic(workload, prec_name, kernel):
+def pass_kernel_source_hash():
+    """SHA-256 of the pass kernel's source: sense_tc.cu up to the end of tc_pass_kernel (its
+    helpers and the kernel itself) followed by sense_tc.cuh."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2604_09233_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in ("sense_tc.cu", "sense_tc.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    rec = KERNEL_TRAFFIC.get(h.hexdigest())
+    with open(os.path.join(csrc, "sense_tc.cu"), "rb") as fh:
+        text = fh.read()
+    end = text.index(b"template <int CP, int RP, int NPART>\nconstexpr size_t smem_bytes()")
+    h = hashlib.sha256(text[:end])
+    with open(os.path.join(csrc, "sense_tc.cuh"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
+def _kernel_traffic(workload, prec_name, kernel):
+    rec = KERNEL_TRAFFIC.get(pass_kernel_source_hash())
     if not rec or rec["workload"] != workload or rec["precision"] != prec_name:
         return None
     return rec.get(kernel)

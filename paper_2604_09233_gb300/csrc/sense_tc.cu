@@ -736,25 +736,33 @@ constexpr size_t smem_bytes() {
 // ---------------------------------------------------------------------------------------
 // B-operand images: per-coil power-of-two scaling, FP16 hi (+ lo), 128B-swizzled rows
 // ---------------------------------------------------------------------------------------
-// colmax[c] = max over the block's rows of max(|re|, |im|) of v(r, c) (float bits, >= 0)
+// colmax[c] = max over the rows of max(|re|, |im|) of v(r, c) (float bits, >= 0): a
+// shared-memory maximum per block, then one global atomic per coil and block
 __global__ void colmax_kernel(const float2* __restrict__ src, const float2* __restrict__ S,
                               const float2* __restrict__ pv, long long nrows, int CP,
                               unsigned* __restrict__ colmax) {
+  __shared__ unsigned sm[64];
+  for (int c = threadIdx.x; c < CP; c += blockDim.x) sm[c] = 0u;
+  __syncthreads();
   const long long n = nrows * CP;
+  // blockDim.x is a multiple of CP, so a thread keeps one coil for its whole stride
+  const int c = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) % CP);
+  float mx = 0.0f;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / CP;
-    const int c = (int)(idx % CP);
     float2 v;
     if (src) {
       v = src[idx];
     } else {
-      const float2 s = S[idx], m = pv[r];
+      const float2 s = S[idx], m = pv[idx / CP];
       v = make_float2(s.x * m.x - s.y * m.y, s.x * m.y + s.y * m.x);
     }
-    const float a = fmaxf(fabsf(v.x), fabsf(v.y));
-    if (a > 0.0f) atomicMax(&colmax[c], __float_as_uint(a));
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
+  if (mx > 0.0f) atomicMax(&sm[c], __float_as_uint(mx));
+  __syncthreads();
+  for (int k = threadIdx.x; k < CP; k += blockDim.x)
+    if (sm[k]) atomicMax(&colmax[k], sm[k]);
 }
 
 // One thread per 16-byte chunk (8 consecutive rows r of one image row n, one part).
@@ -982,7 +990,13 @@ __global__ void tc_reduce_y_kernel(const float2* __restrict__ Ypart, const int* 
                                    float2* __restrict__ Y, float2* __restrict__ su,
                                    unsigned* __restrict__ colmax, const double* __restrict__ stop) {
   if (stop && *stop != 0.0) return;
+  __shared__ unsigned sm[64];
+  if (colmax) {
+    for (int c = threadIdx.x; c < Cp; c += blockDim.x) sm[c] = 0u;
+    __syncthreads();
+  }
   const long long n = Kp * Cp;
+  float mx = 0.0f;   // blockDim.x is a multiple of Cp: one coil per thread
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const long long k = i / Cp;
@@ -998,10 +1012,15 @@ __global__ void tc_reduce_y_kernel(const float2* __restrict__ Ypart, const int* 
     }
     if (Y) Y[i] = a;
     if (su && k < K && c < C) su[k * C + c] = a;
-    if (colmax) {
-      const float m = fmaxf(fabsf(a.x), fabsf(a.y));
-      if (m > 0.0f) atomicMax(&colmax[c], __float_as_uint(m));
-    }
+    mx = fmaxf(mx, fmaxf(fabsf(a.x), fabsf(a.y)));
+  }
+  if (colmax) {
+    if (mx > 0.0f)
+      atomicMax(&sm[(int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) % Cp)],
+                __float_as_uint(mx));
+    __syncthreads();
+    for (int k = threadIdx.x; k < Cp; k += blockDim.x)
+      if (sm[k]) atomicMax(&colmax[k], sm[k]);
   }
 }
 
