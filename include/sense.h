@@ -220,7 +220,8 @@ int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const doub
  *
  * sense_batch_create: probs[n] as for sense_plan_create (host arrays, copied). The batch
  *   owns one plan per instance; sense_batch_plan returns it (borrowed: do not destroy) for
- *   single-instance calls. Errors as sense_plan_create, EINVAL for n < 1.
+ *   single-instance calls; after sense_plan_set_b0 on a member plan the next batch call
+ *   rebuilds the batch's descriptors. Errors as sense_plan_create, EINVAL for n < 1.
  * sense_batch_info: out = {n, padded coils, delta rows, chunk}.
  * sense_batch_normal_op: out[b] = E_b^H E_b m[b] for every b ([L_b] complex64, device).
  * sense_batch_cg_solve: sense_cg_solve for every instance with the same options (history

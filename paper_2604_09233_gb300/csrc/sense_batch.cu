@@ -36,6 +36,7 @@ struct sense_batch_s {
   std::vector<int*> nslot_e, nslot_a;  // per instance, per row block: nchunk
   cudaGraphExec_t gexec = nullptr;
   int graph_prec = -1;
+  std::vector<int64_t> geom_versions;  // of each plan when the descriptors were built
 };
 
 namespace sense {
@@ -79,6 +80,13 @@ void free_layout(sense_batch_s* B) {
 int build_layout(sense_batch_s* B) {
   free_layout(B);
   const int n = (int)B->plans.size();
+  B->geom_versions.clear();
+  for (auto* P : B->plans) {
+    // a rebuilt geometry (sense_plan_set_b0 on a member plan) must keep the batch layout
+    if (P->Cp != B->Cp || P->RT != B->RT)
+      return set_error(SENSE_EUNSUPPORTED, "a member plan left the batch-wide layout");
+    B->geom_versions.push_back(P->geom_version);
+  }
   const int CH = B->chunk;
   std::vector<int4> it[2];
   std::vector<tc::InstDesc> d[2][2];
@@ -224,6 +232,13 @@ int check_batch(sense_batch_s* B) {
   int dev = -1;
   SENSE_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != B->device) return set_error(SENSE_EINVAL, "batch belongs to another device");
+  // the descriptors hold the plans' geometry pointers: rebuild them after a member plan's
+  // geometry was rebuilt (its B0 map replaced)
+  for (size_t b = 0; b < B->plans.size(); ++b)
+    if (b >= B->geom_versions.size() || B->plans[b]->geom_version != B->geom_versions[b]) {
+      SENSE_CUDA_TRY(cudaDeviceSynchronize());
+      return build_layout(B);
+    }
   return SENSE_OK;
 }
 

@@ -108,6 +108,7 @@ struct sense_plan_s {
   int tc_grid_req = 0;             // requested CTAs (one per SM by default)
   int tc_seg_len = 4;              // drain the TMEM accumulators every this many pairs
   int min_rt = 0;                  // lower bound on RT (uniform kernels across a batch)
+  int64_t geom_version = 0;        // incremented whenever the geometry arrays are rebuilt
   int tc_slots_e = 1, tc_slots_a = 1;
   int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E
   int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [nvb] stream-K slots of E^H

@@ -235,6 +235,7 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   }
 
   free_geometry(P);
+  ++P->geom_version;
   SENSE_TRY(dalloc(&P->dKd, (size_t)Kp * P1));
   SENSE_TRY(dalloc(&P->dRd, (size_t)P1 * Lp));
   SENSE_TRY(dalloc(&P->dKc, (size_t)P->nsb * P1));

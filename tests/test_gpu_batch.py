@@ -102,6 +102,30 @@ def test_batch_cg_stops_each_instance_like_the_single_path(small):
         assert iters[i] == n or (ambiguous and abs(iters[i] - n) <= 1)
 
 
+def test_batch_follows_a_member_plans_new_b0_map(small):
+    """Replacing a member plan's B0 map rebuilds that plan's geometry; the batch picks up the
+    new arrays on its next call (its descriptors would otherwise point at the old ones)."""
+    import torch
+    from paper_2604_09233_gb300 import native
+    wls, b = small
+    dev = torch.device("cuda:0")
+    i = 2
+    w = wls[i]
+    Rm = w.Rmat.copy()
+    Rm[0] = 1.5 * Rm[0] + 40.0
+    native.sense_plan_set_b0(native.sense_batch_plan(b.handle, i), Rm[0])
+    try:
+        rng = np.random.default_rng(24)
+        ms = [_crandn(rng, x.L).astype(np.complex64) for x in wls]
+        outs = b.normal([torch.from_numpy(m).to(dev) for m in ms])
+        ref = oracle.normal(w.Kmat, Rm, w.S, ms[i], j=w.j)
+        assert _rel(outs[i].cpu().numpy(), ref) <= TOL["tc_split"]
+        assert _rel(outs[0].cpu().numpy(), oracle.normal(wls[0].Kmat, wls[0].Rmat, wls[0].S,
+                                                          ms[0], j=wls[0].j)) <= TOL["tc_split"]
+    finally:
+        native.sense_plan_set_b0(native.sense_batch_plan(b.handle, i), w.Rmat[0])
+
+
 def test_batch_graph_replay_is_deterministic(small):
     import torch
     wls, b = small
