@@ -43,6 +43,8 @@ def _parse():
     ap.add_argument("--workload", default="target_256",
                     choices=["target_256", "precision_128", "plain_32", "stack_3d", "batch_64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="skip the (untimed) differentiation measurements")
     ap.add_argument("--op-only", action="store_true",
                     help="time only W + K single E^H E applies (used for kernel profiling)")
     return ap.parse_args()
@@ -393,6 +395,39 @@ def run_ours(args):
     e2e_value = job_rate(n_it * len(e2e_t), world,
                          max_over_ranks(1e3 * float(np.sum(e2e_t)), world, dev))
 
+    # ---------------------------------------------------------------- differentiation (untimed)
+    # 40-iteration CG with checkpoints every 8 iterations, its reverse pass (ds and d omega of
+    # Re<w, x>), and the B0-gradient primitive of E (one t-weighted adjoint plus E^H g)
+    diff = None
+    if not args.no_grad:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        nbytes = native.sense_cg_ckpt_bytes(plan.handle, n_it, 8)
+        ck = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        xg = torch.empty_like(x)
+        sbar = torch.empty_like(s)
+        wbar = torch.empty(wl.L, dtype=torch.float32, device=dev)
+        xbar = torch.ones_like(x)
+        native.sense_cg_solve_ckpt(plan.handle, s, xg, ck, n_it, 8, prec=prec)   # warm-up
+        native.sense_cg_backward(plan.handle, s, ck, xbar, sbar=sbar, omega_bar=wbar)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        native.sense_cg_solve_ckpt(plan.handle, s, xg, ck, n_it, 8, prec=prec)
+        ev[1].record(stream)
+        native.sense_cg_backward(plan.handle, s, ck, xbar, sbar=sbar, omega_bar=wbar)
+        ev[2].record(stream)
+        gw = torch.empty(wl.L, dtype=torch.float32, device=dev)
+        gz = torch.empty_like(x)
+        native.sense_grad_b0(plan.handle, prec, m, s, gw, z=gz)
+        ev[3].record(stream)
+        native.sense_grad_b0(plan.handle, prec, m, s, gw, z=gz)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        diff = {"cg_iters": n_it, "ckpt_every": 8, "forward_ms": fwd, "backward_ms": bwd,
+                "backward_over_forward": bwd / fwd, "grad_b0_primitive_ms": ev[3].elapsed_time(ev[4]),
+                "checkpoint_bytes": nbytes,
+                "finite": bool(torch.isfinite(wbar).all().item() and torch.isfinite(sbar).all().item())}
+
     # ---------------------------------------------------------------- roofline
     # dominant kernel: the tensor-core pass (E or E^H) with the larger share of event time
     peaks, peak_kind = _peaks()
@@ -437,6 +472,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": wl.L * 8},
         "gpu_launches": stats["launches"],
     }
+    if diff is not None:
+        line["differentiation"] = diff
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_apply_rate(wl)
         cb.pop("seconds")
