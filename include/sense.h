@@ -143,6 +143,16 @@ typedef struct {
 int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opts* opts,
                    double* history, sense_cg_info* info, void* stream);
 
+/* sense_cg_solve that also records every iterate: iterates is DEVICE memory of
+ * (max_iter + 1) x L complex64, row n = rho_n in user voxel order (multiplied by j when
+ * apply_j, like the result); row 0 is zero and rows after a tolerance stop repeat the final
+ * iterate; the result itself is row max_iter. Used to study stopping rules against a known
+ * image (the paper compares the L-curve corner with SSIM over the iterations). Errors as
+ * sense_cg_solve, plus EINVAL for host memory. */
+int sense_cg_solve_iterates(sense_plan plan, const float* s, float* iterates,
+                            const sense_cg_opts* opts, double* history, sense_cg_info* info,
+                            void* stream);
+
 /* Maximum-curvature (L-curve corner) index over history rows 1..n-1 of a CG history
  * (format of sense_cg_solve): points (log ||E x_n - s||, log ||x_n||), curvature signed
  * positive for the clockwise turn at the corner, central differences; first maximum

@@ -464,6 +464,21 @@ extern "C" int sense_normal_op(sense_plan P, int prec, const float* m, float* o,
   return out.host && prec != SENSE_PREC_FP32 ? tc_check_error(P) : SENSE_OK;
 }
 
+extern "C" int sense_cg_solve_iterates(sense_plan P, const float* s, float* iterates,
+                                       const sense_cg_opts* opts, double* history,
+                                       sense_cg_info* info, void* stream) {
+  TRY(check_plan(P));
+  if (!s || !iterates || !opts) return set_error(SENSE_EINVAL, "null s, iterates or opts");
+  if (opts->max_iter < 0 || !(opts->rel_tol >= 0.0) || opts->refine_every < 0)
+    return set_error(SENSE_EINVAL, "max_iter, rel_tol and refine_every must be >= 0");
+  TRY(check_prec(opts->prec));
+  if (!is_device_pointer(iterates)) return set_error(SENSE_EINVAL, "iterates must be device memory");
+  float2* X = (float2*)iterates;
+  // the final iterate is row max_iter
+  return cg_run(P, s, (float*)(X + (size_t)opts->max_iter * P->L), opts, history, info, 0,
+                nullptr, X, (cudaStream_t)stream);
+}
+
 extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sense_cg_opts* opts,
                               double* history, sense_cg_info* info, void* stream) {
   TRY(check_plan(P));
@@ -471,7 +486,7 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
   if (opts->max_iter < 0 || !(opts->rel_tol >= 0.0) || opts->refine_every < 0)
     return set_error(SENSE_EINVAL, "max_iter, rel_tol and refine_every must be >= 0");
   TRY(check_prec(opts->prec));
-  return cg_run(P, s, x, opts, history, info, 0, nullptr, (cudaStream_t)stream);
+  return cg_run(P, s, x, opts, history, info, 0, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 namespace sense {
@@ -519,7 +534,7 @@ int cg_read_info(sense_plan_s* P, sense_cg_info* info, int* iters, cudaStream_t 
 
 int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
            double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
-           cudaStream_t st) {
+           float2* iterates, cudaStream_t st) {
   const int N = opts->max_iter;
   if (N + 1 > P->max_hist) {
     cudaFree(P->hist);
@@ -537,6 +552,7 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
   const int vb = grid_for(P, P->Lp);
   TRY(cg_begin(P, (const float2*)in.dev, opts, P->hist, st));
   const double* stop = P->scal + SC_STOP;
+  if (iterates) SENSE_CUDA_TRY(cudaMemsetAsync(iterates, 0, (size_t)P->L * 8, st));
   for (int n = 0; n < N; ++n) {
     if (ckpt_every > 0 && n % ckpt_every == 0) TRY(ckpt_save(P, ckpt, n / ckpt_every, st));
     // step 8
@@ -553,6 +569,9 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
       count_launch(P);
     }
     TRY(cg_step_p(P, st));
+    // x_{n+1} in user order (after the stop it repeats the final iterate)
+    if (iterates)
+      TRY(scatter_image(P, P->vx, iterates + (size_t)(n + 1) * P->L, opts->apply_j != 0, st));
   }
   if (ckpt_every > 0) TRY(ckpt_final(P, ckpt, st));
   // step 18

@@ -430,7 +430,7 @@ extern "C" int sense_cg_solve_ckpt(sense_plan P, const float* s, float* x,
   h.nck = ckpt_count(opts->max_iter, ckpt_every);
   // pageable source: the copy has read h when the call returns
   SENSE_CUDA_TRY(cudaMemcpyAsync(ckpt, &h, sizeof(h), cudaMemcpyHostToDevice, st));
-  return cg_run(P, s, x, opts, nullptr, info, ckpt_every, (uint8_t*)ckpt, st);
+  return cg_run(P, s, x, opts, nullptr, info, ckpt_every, (uint8_t*)ckpt, nullptr, st);
 }
 
 extern "C" int sense_cg_backward(sense_plan P, const float* s, const void* ckpt,

@@ -209,10 +209,11 @@ int check_plan(sense_plan_s* P);
 int check_prec(int prec);
 int grid_for(sense_plan_s* P, int64_t n);
 // One CG solve; with ckpt_every > 0 the state (r, p, scalars) before every ckpt_every-th
-// iteration and the final scalars are written to ckpt (layout of sense_grad.cu).
+// iteration and the final scalars are written to ckpt (layout of sense_grad.cu); with
+// iterates, every x_n (n = 0..max_iter, user order) to iterates[n].
 int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
            double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
-           cudaStream_t st);
+           float2* iterates, cudaStream_t st);
 int cg_begin(sense_plan_s* P, const float2* s_dev, const sense_cg_opts* opts, double* hist,
              cudaStream_t st);
 int cg_read_info(sense_plan_s* P, sense_cg_info* info, int* iters, cudaStream_t st);

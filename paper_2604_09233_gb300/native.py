@@ -32,7 +32,7 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_grad_b0", "sense_cg_ckpt_bytes", "sense_cg_solve_ckpt", "sense_cg_backward",
             "sense_batch_create", "sense_batch_destroy", "sense_batch_plan", "sense_batch_info",
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
-            "sense_batch_autotune"]
+            "sense_batch_autotune", "sense_cg_solve_iterates"]
 
 
 class SenseError(RuntimeError):
@@ -89,6 +89,8 @@ def _load():
         "sense_cg_solve": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp, ctypes.POINTER(CGInfo), vp],
                            ctypes.c_int),
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "sense_cg_solve_iterates": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp,
+                                     ctypes.POINTER(CGInfo), vp], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
         "sense_plan_sync": ([vp, vp], ctypes.c_int),
         "sense_encode_noalloc": ([i64, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -230,6 +232,23 @@ def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refi
                                _stream(ss, sx, explicit=stream)), "sense_cg_solve")
     out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
     return out, (None if hist is None else hist[: info.iters + 1])
+
+
+def sense_cg_solve_iterates(plan, s, iterates, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0,
+                            refine_every=0, apply_j=True, stream=None):
+    """CG recording every iterate into iterates ([max_iter+1][L] complex64 CUDA tensor).
+    Returns (info dict, history array [iters+1][3])."""
+    ps, _, ss = _ptr(s)
+    pX, _, sX = _ptr(iterates)
+    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), int(refine_every),
+                  1 if apply_j else 0)
+    info = CGInfo()
+    hist = np.full((int(max_iter) + 1, 3), np.nan)
+    _check(_lib.sense_cg_solve_iterates(plan, ps, pX, ctypes.byref(opts), hist.ctypes.data,
+                                        ctypes.byref(info), _stream(ss, sX, explicit=stream)),
+           "sense_cg_solve_iterates")
+    out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
+    return out, hist[: info.iters + 1]
 
 
 def sense_encode_noalloc(Kmat, Rmat, S, m, s, j=None, stream=None):
