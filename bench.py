@@ -428,6 +428,29 @@ def run_ours(args):
                 "checkpoint_bytes": nbytes,
                 "finite": bool(torch.isfinite(wbar).all().item() and torch.isfinite(sbar).all().item())}
 
+    # ---------------------------------------------------------------- k-space filter (untimed)
+    # Fig. 2 Alg. 1 step 19 on the reconstructed image (2D workloads): convex-hull mask of the
+    # first-order coefficients (host, once) and the filter (device)
+    kfilter = None
+    if len(wl.shape) == 2:
+        N = wl.shape[0]
+        d = wl.meta["fov"] / N
+        cx = 1 if wl.Kmat.shape[1] == 3 else 2          # columns of (kx, ky) in K
+        t0 = time.perf_counter()
+        mask = native.sense_kspace_filter_mask(N, N, d, d, wl.Kmat[:, cx], wl.Kmat[:, cx + 1])
+        t_mask = time.perf_counter() - t0
+        mk = torch.from_numpy(mask.ravel()).to(dev)
+        img = x_tc.clone()
+        native.sense_kspace_filter(img, mk, wl.shape)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(3):
+            native.sense_kspace_filter(img, mk, wl.shape)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        kfilter = {"filter_ms": ev[0].elapsed_time(ev[1]) / 3, "mask_host_ms": 1e3 * t_mask,
+                   "mask_fraction": float(mask.mean())}
+
     # ---------------------------------------------------------------- roofline
     # dominant kernel: the tensor-core pass (E or E^H) with the larger share of event time
     peaks, peak_kind = _peaks()
@@ -474,6 +497,8 @@ def run_ours(args):
     }
     if diff is not None:
         line["differentiation"] = diff
+    if kfilter is not None:
+        line["kspace_filter"] = kfilter
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_apply_rate(wl)
         cb.pop("seconds")

@@ -218,6 +218,22 @@ int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const doub
                          const double* Rmat, const float* S, const float* j, const float* m,
                          float* s, void* stream);
 
+/* k-space filter (Fig. 2 Alg. 1 step 19: rho = IFFT(FFT(rho) o f)) -------------------------
+ * sense_kspace_filter_mask (host only): f for an nx x ny grid of spacing dx, dy (m): 1 for the
+ *   Cartesian k-space points k = 2 pi (u - n/2) / (n d) inside (or on) the convex hull of the
+ *   K first-order coefficients (kx, ky) (rad/m) of the samples, else 0; mask [ny][nx] host
+ *   float. 2D only (a 3D hull is not implemented). Errors: EINVAL, ENONFINITE.
+ * sense_kspace_filter: image [nz][ny][nx] complex64 (DEVICE, raster order = the user voxel
+ *   order of a full-grid problem) filtered in place with mask [nz][ny][nx] float (DEVICE),
+ *   using the signal model's sign: F(k_u) = sum_x rho(x) e^{+i k_u r_x}, r_x = (x - n/2) d,
+ *   then rho(x) = (1/n) sum_u F(k_u) f(u) e^{-i k_u r_x} along every axis of length > 1
+ *   (any length up to 4096; a mask of ones returns the image). Synchronises the stream.
+ *   Errors: EINVAL, ENOMEM, ECUDA. */
+int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, double dy, const double* kx,
+                             const double* ky, int64_t K, float* mask);
+int sense_kspace_filter(int32_t nx, int32_t ny, int32_t nz, const float* mask, float* image,
+                        void* stream);
+
 /* Batched reconstruction -----------------------------------------------------------------
  * (no counterpart in the paper, which reconstructs one slice or volume at a time)
  * A batch holds n independent problems of uneven size (voxels, samples, coils, basis rows)

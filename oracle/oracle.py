@@ -171,6 +171,39 @@ def grad_omega_adjoint(Kmat, Rmat, S, y, h, j=None):
     return out
 
 
+def kspace_mask(nx, ny, dx, dy, kx, ky):
+    """k-space filter of the paper's k-space filter section: 1 for the Cartesian k-space
+    points 2 pi (u - n/2) / (n d) that lie in a triangle of the Delaunay triangulation of the
+    first-order k-space coordinates (kx, ky), else 0 ([ny][nx])."""
+    from scipy.spatial import Delaunay
+    tri = Delaunay(np.stack([np.asarray(kx, float), np.asarray(ky, float)], axis=1))
+    u = 2 * np.pi * (np.arange(nx) - nx // 2) / (nx * dx)
+    v = 2 * np.pi * (np.arange(ny) - ny // 2) / (ny * dy)
+    U, V = np.meshgrid(u, v)
+    inside = tri.find_simplex(np.stack([U.ravel(), V.ravel()], axis=1)) >= 0
+    return inside.reshape(ny, nx).astype(np.float64)
+
+
+def kspace_filter(image, shape, mask):
+    """rho <- IFFT(FFT(rho) o f) (Fig. 2 Alg. 1 step 19) with the signal model's sign along every
+    axis: F(k_u) = sum_x rho(x) e^{+i 2 pi (u - n/2)(x - n/2) / n}, then
+    rho(x) = (1/n) sum_u F(k_u) f(u) e^{-i 2 pi (u - n/2)(x - n/2) / n}, written out as dense
+    matrices (shape: (ny, nx) or (nz, ny, nx))."""
+    x = np.asarray(image, np.complex128).reshape(shape)
+    f = np.asarray(mask, np.float64).reshape(shape)
+
+    def W(n, sgn):
+        c = np.arange(n) - n // 2
+        return np.exp(sgn * 2j * np.pi * np.outer(c, c) / n)
+
+    for ax, n in enumerate(shape):
+        x = np.moveaxis(np.tensordot(W(n, +1), np.moveaxis(x, ax, 0), axes=(1, 0)), 0, ax)
+    x = x * f
+    for ax, n in enumerate(shape):
+        x = np.moveaxis(np.tensordot(W(n, -1), np.moveaxis(x, ax, 0), axes=(1, 0)) / n, 0, ax)
+    return x.ravel()
+
+
 def lcurve_corner(res_norm, sol_norm):
     """Index n (into the given arrays) of maximum L-curve curvature.
 

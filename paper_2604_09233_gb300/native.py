@@ -32,7 +32,8 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_grad_b0", "sense_cg_ckpt_bytes", "sense_cg_solve_ckpt", "sense_cg_backward",
             "sense_batch_create", "sense_batch_destroy", "sense_batch_plan", "sense_batch_info",
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
-            "sense_batch_autotune", "sense_cg_solve_iterates"]
+            "sense_batch_autotune", "sense_cg_solve_iterates", "sense_kspace_filter_mask",
+            "sense_kspace_filter"]
 
 
 class SenseError(RuntimeError):
@@ -89,6 +90,8 @@ def _load():
         "sense_cg_solve": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp, ctypes.POINTER(CGInfo), vp],
                            ctypes.c_int),
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "sense_kspace_filter_mask": ([i32, i32, dbl, dbl, vp, vp, i64, vp], ctypes.c_int),
+        "sense_kspace_filter": ([i32, i32, i32, vp, vp, vp], ctypes.c_int),
         "sense_cg_solve_iterates": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp,
                                      ctypes.POINTER(CGInfo), vp], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
@@ -249,6 +252,29 @@ def sense_cg_solve_iterates(plan, s, iterates, max_iter, prec=SENSE_PREC_FP32, r
            "sense_cg_solve_iterates")
     out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
     return out, hist[: info.iters + 1]
+
+
+def sense_kspace_filter_mask(nx, ny, dx, dy, kx, ky):
+    """Convex-hull k-space filter [ny][nx] (float32 numpy) from first-order coefficients."""
+    kx = np.ascontiguousarray(kx, np.float64)
+    ky = np.ascontiguousarray(ky, np.float64)
+    if kx.shape != ky.shape:
+        raise ValueError("kx and ky differ in shape")
+    mask = np.empty((int(ny), int(nx)), np.float32)
+    _check(_lib.sense_kspace_filter_mask(int(nx), int(ny), float(dx), float(dy), kx.ctypes.data,
+                                         ky.ctypes.data, int(kx.size), mask.ctypes.data),
+           "sense_kspace_filter_mask")
+    return mask
+
+
+def sense_kspace_filter(image, mask, shape, stream=None):
+    """Filter a complex64 CUDA image of `shape` ((ny, nx) or (nz, ny, nx)) in place with a
+    float32 CUDA mask of the same shape."""
+    nz, ny, nx = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
+    pi, _, si = _ptr(image)
+    pm, _, _ = _ptr(mask, np.float32)
+    _check(_lib.sense_kspace_filter(int(nx), int(ny), int(nz), pm, pi,
+                                    _stream(si, explicit=stream)), "sense_kspace_filter")
 
 
 def sense_encode_noalloc(Kmat, Rmat, S, m, s, j=None, stream=None):

@@ -248,3 +248,42 @@ def test_lcurve_corner_on_parabola_vertex():
     xs2 = xs + 0.5                             # vertex now where xs == -0.5 -> index 25
     assert oracle.lcurve_corner(np.exp(xs2), np.exp((xs2 - 0.0) ** 2)) == 25
     assert oracle.lcurve_corner([1.0, 2.0], [1.0, 1.0]) == -1
+
+
+def test_kspace_filter_keeps_inside_and_removes_outside_plane_waves():
+    """A Cartesian plane wave rho(x) = e^{-i k_u r_x} has all of its k-space content at k_u:
+    the filter returns it unchanged when f(u) = 1 and removes it when f(u) = 0; f = 1 is the
+    identity; the transform is linear (checked on a sum)."""
+    shape = (6, 10)
+    ny, nx = shape
+    y, x = np.mgrid[:ny, :nx]
+    f = np.zeros(shape)
+    f[2, 7] = 1.0
+
+    def wave(u, v):
+        return np.exp(-2j * np.pi * ((u - nx // 2) * (x - nx // 2) / nx
+                                     + (v - ny // 2) * (y - ny // 2) / ny)).ravel()
+
+    a, b = wave(7, 2), wave(3, 4)
+    assert np.allclose(oracle.kspace_filter(a, shape, f), a, atol=1e-12)
+    assert np.allclose(oracle.kspace_filter(b, shape, f), 0, atol=1e-12)
+    assert np.allclose(oracle.kspace_filter(2 * a + b, shape, f), 2 * a, atol=1e-12)
+    rng = np.random.default_rng(6)
+    z = rng.normal(size=60) + 1j * rng.normal(size=60)
+    assert np.allclose(oracle.kspace_filter(z, shape, np.ones(shape)), z, atol=1e-12)
+    # 3D: the same along the third axis
+    z3 = rng.normal(size=(3, 4, 5)) + 1j * rng.normal(size=(3, 4, 5))
+    assert np.allclose(oracle.kspace_filter(z3, (3, 4, 5), np.ones((3, 4, 5))), z3.ravel())
+
+
+def test_kspace_mask_of_a_square_of_samples():
+    """Samples on the corners of a square cover exactly the Cartesian points inside it."""
+    nx = ny = 8
+    d = 0.01
+    dk = 2 * np.pi / (nx * d)
+    kx = np.array([-2.5, 2.5, 2.5, -2.5]) * dk
+    ky = np.array([-1.5, -1.5, 1.5, 1.5]) * dk
+    m = oracle.kspace_mask(nx, ny, d, d, kx, ky)
+    expect = np.zeros((ny, nx))
+    expect[4 - 1: 4 + 2, 4 - 2: 4 + 3] = 1.0
+    assert np.array_equal(m, expect)
