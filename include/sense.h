@@ -273,6 +273,15 @@ int sense_batch_set_tuning(sense_batch batch, int32_t chunk, int32_t seg_len);
 int sense_batch_autotune(sense_batch batch, int32_t prec, int32_t* chunk, int32_t* seg_len,
                          double* ms);
 
+/* Stored-P mode (the paper's Alg. 1 choice, offered as a comparison to on-the-fly generation).
+ * enable != 0: compute the phase tiles of both passes once (FP16 hi and lo, 8 bytes per
+ * (sample, voxel) pair and pass: 2 x 8 x L_p x K_p bytes, 37.6 GB at 256 x 256 and 35750 samples)
+ * and from then on stream them from HBM in the tensor-core passes instead of generating them;
+ * results are bit-identical in TC_SPLIT mode (TC_FP16 uses the split's hi part). enable == 0
+ * frees them. sense_plan_set_b0 regenerates them. Synchronises the stream. Errors: EINVAL,
+ * ENOMEM (the tiles do not fit), ECUDA. */
+int sense_plan_store_p(sense_plan plan, int32_t enable, void* stream);
+
 /* Tuning ------------------------------------------------------------------------------
  * (no counterpart in the paper: execution parameters of the tensor-core kernels)
  *   seg_len  the tensor-core passes accumulate at most this many 128 x 128 (sample, voxel)

@@ -119,6 +119,8 @@ struct sense_plan_s {
   float2* Ypart_tc = nullptr;      // [tc_slots_e][Kp][Cp]
   float2* Xpart_tc = nullptr;      // [tc_slots_a][Lp]
   int* tc_err = nullptr;           // time-out word written by the tensor-core kernels
+  uint4* p_enc = nullptr;          // stored-P mode: phase tiles of the E pass
+  uint4* p_adj = nullptr;          // and of the E^H pass (conjugated, transposed)
 
   // gradient workspace (sense_grad.cu), allocated on first use
   float2* Yg = nullptr;            // [Kp][Cp] E of an adjoint vector

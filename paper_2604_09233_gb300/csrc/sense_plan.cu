@@ -16,7 +16,7 @@
 #include <cstring>
 #include <numeric>
 
-#include "sense_internal.cuh"
+#include "sense_tc.cuh"
 
 namespace sense {
 
@@ -455,7 +455,10 @@ extern "C" int sense_plan_set_b0(sense_plan P, const double* omega, void* stream
   cudaStream_t st = (cudaStream_t)stream;
   SENSE_CUDA_TRY(cudaStreamSynchronize(st));
   std::copy(omega, omega + P->L, P->Rh.begin());
-  return build_geometry(P, st);
+  const int rc = build_geometry(P, st);
+  // stored phase tiles follow the new geometry
+  if (rc != SENSE_OK || !P->p_enc) return rc;
+  return tc_store_p(P, true, st);
 }
 
 extern "C" int sense_plan_info(sense_plan P, int64_t out[8]) {

@@ -244,9 +244,11 @@ struct Smem {
   static constexpr int NBUFS = CP <= 32 ? 3 : 2;
 };
 
-template <int MODE, int CP, int RT, int NPART>
+template <int MODE, int CP, int RT, int NPART, bool STORED>
 // 18 warps: up to 5 on one SM sub-partition, whose register file holds 16K registers, so
-// 96 registers per thread is the ceiling; one CTA per SM.
+// 96 registers per thread is the ceiling; one CTA per SM. STORED: the generator warps copy
+// precomputed phase tiles from HBM into tensor memory instead of computing them (the loader
+// then brings only the B image).
 __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
   using SM = Smem<CP, NPART>;
   constexpr int NBUF = SM::NBUFS;
@@ -355,15 +357,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           mbar_arrive(fb);
         } else {
           const InstDesc& d = desc(b);
-          mbar_arrive_expect_tx(fb, SM::B_BYTES + col_bytes + 1024u);
+          mbar_arrive_expect_tx(fb, SM::B_BYTES + (STORED ? 0u : col_bytes + 1024u));
           bulk_g2s(smem_u32(sB + buf * SM::B_BYTES), d.Bimg + (long long)in * SM::B_BYTES,
                    SM::B_BYTES, fb);
-          bulk_g2s(smem_u32(sCol + buf * 128 * RT), d.colT + (long long)in * 128 * RT,
-                   col_bytes, fb);
-          bulk_g2s(smem_u32(sAnc + buf * 128), d.colAnc + (long long)o * d.cols_total + in * 128,
-                   512u, fb);
-          bulk_g2s(smem_u32(sRowAnc + buf * 128),
-                   d.rowAnc + (long long)in * d.rows_total + (long long)o * 128, 512u, fb);
+          if (!STORED) {
+            bulk_g2s(smem_u32(sCol + buf * 128 * RT), d.colT + (long long)in * 128 * RT,
+                     col_bytes, fb);
+            bulk_g2s(smem_u32(sAnc + buf * 128),
+                     d.colAnc + (long long)o * d.cols_total + in * 128, 512u, fb);
+            bulk_g2s(smem_u32(sRowAnc + buf * 128),
+                     d.rowAnc + (long long)in * d.rows_total + (long long)o * 128, 512u, fb);
+          }
         }
         ++it;
         return true;
@@ -606,13 +610,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       if (m.flags & META_FIRST) run_pos = 0;
       const bool seg_last = (m.flags & META_LAST) || ((run_pos + 1) % F == 0);
       ++run_pos;
-      if (m.o != cur_o || m.inst != cur_b) {
+      if (!STORED && (m.o != cur_o || m.inst != cur_b)) {
         cur_o = m.o;
         cur_b = m.inst;
         const float* rT = desc(cur_b).rowT;
 #pragma unroll
         for (int q = 0; q < RT; ++q) own[q] = rT[((long long)cur_o * RT + q) * 128 + row];
       }
+      // stored tiles of this pair: 16 chunks of [4][128] uint4
+      const uint4* ptile =
+          STORED ? desc(m.inst).stored +
+                       ((long long)m.o * desc(m.inst).n_inner + m.in) * (16 * 4 * 128) + row
+                 : nullptr;
       const float* col = sCol + buf * 128 * RT;
       const float* anc = sAnc + buf * 128;
       const float rb = sRowAnc[buf * 128 + row];
@@ -628,6 +637,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         tc_fence_after();
         const int c0 = st * 64 + g * 16;
         const uint32_t acol = tmem + lane_base + SM::ACOL0 + slot * (NPART * 64) + g * 8;
+        if (STORED) {
+          // both halves' tiles, loaded before any of them is stored: 2 x (4 | 2) x 16 B
+          uint4 v[2][4];
+#pragma unroll
+          for (int jh = 0; jh < 2; ++jh) {
+            const uint4* c = ptile + (((st * 4 + g) * 2 + jh) * 4) * 128;
+            v[jh][0] = __ldg(c);
+            v[jh][2] = __ldg(c + 2 * 128);
+            if (NPART == 2) {
+              v[jh][1] = __ldg(c + 128);
+              v[jh][3] = __ldg(c + 3 * 128);
+            }
+          }
+#pragma unroll
+          for (int jh = 0; jh < 2; ++jh) {
+            const uint32_t re_hi[4] = {v[jh][0].x, v[jh][0].y, v[jh][0].z, v[jh][0].w};
+            const uint32_t im_hi[4] = {v[jh][2].x, v[jh][2].y, v[jh][2].z, v[jh][2].w};
+            __syncwarp();
+            if (jh == 0) flush_pending();
+            const uint32_t hc = acol + 4 * jh;
+            if (NPART == 2) {
+              const uint32_t re_lo[4] = {v[jh][1].x, v[jh][1].y, v[jh][1].z, v[jh][1].w};
+              const uint32_t im_lo[4] = {v[jh][3].x, v[jh][3].y, v[jh][3].z, v[jh][3].w};
+              tmem_st4(hc + 0, re_hi);
+              tmem_st4(hc + 32, re_lo);
+              tmem_st4(hc + 64, im_hi);
+              tmem_st4(hc + 96, im_lo);
+            } else {
+              tmem_st4(hc + 0, re_hi);
+              tmem_st4(hc + 32, im_hi);
+            }
+          }
+        } else
         // two halves of 8 streamed elements (4 TMEM columns per matrix each)
 #pragma unroll
         for (int jh = 0; jh < 2; ++jh) {
@@ -847,10 +889,10 @@ static int stream_k_layout(long long n_outer, long long n_inner, int G, std::vec
   return SENSE_OK;
 }
 
-template <int MODE, int CP, int RP, int NPART>
+template <int MODE, int CP, int RP, int NPART, bool STORED = false>
 static int launch_pass(sense_plan_s* P, const tc::Params& prm, int G, cudaStream_t st) {
   constexpr size_t smem = tc::smem_bytes<CP, RP, NPART>();
-  auto kern = tc::tc_pass_kernel<MODE, CP, RP, NPART>;
+  auto kern = tc::tc_pass_kernel<MODE, CP, RP, NPART, STORED>;
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     SENSE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -866,7 +908,10 @@ static int launch_pass(sense_plan_s* P, const tc::Params& prm, int G, cudaStream
 }
 
 template <int MODE, int CP, int NPART>
-static int dispatch_rp(sense_plan_s* P, int rt, const tc::Params& prm, int G, cudaStream_t st) {
+static int dispatch_rp(sense_plan_s* P, int rt, const tc::Params& prm, int G, cudaStream_t st,
+                       bool stored) {
+  // the stored-tile kernel computes no phases: one instantiation serves every row count
+  if (stored) return launch_pass<MODE, CP, 4, NPART, true>(P, prm, G, st);
   switch (rt) {
     case 4: return launch_pass<MODE, CP, 4, NPART>(P, prm, G, st);
     case 6: return launch_pass<MODE, CP, 6, NPART>(P, prm, G, st);
@@ -881,23 +926,23 @@ static int dispatch_rp(sense_plan_s* P, int rt, const tc::Params& prm, int G, cu
 
 template <int MODE, int NPART>
 static int dispatch_cp(sense_plan_s* P, int cp, int rt, const tc::Params& prm, int G,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool stored) {
   switch (cp) {
-    case 8: return dispatch_rp<MODE, 8, NPART>(P, rt, prm, G, st);
-    case 16: return dispatch_rp<MODE, 16, NPART>(P, rt, prm, G, st);
-    case 32: return dispatch_rp<MODE, 32, NPART>(P, rt, prm, G, st);
-    case 64: return dispatch_rp<MODE, 64, NPART>(P, rt, prm, G, st);
+    case 8: return dispatch_rp<MODE, 8, NPART>(P, rt, prm, G, st, stored);
+    case 16: return dispatch_rp<MODE, 16, NPART>(P, rt, prm, G, st, stored);
+    case 32: return dispatch_rp<MODE, 32, NPART>(P, rt, prm, G, st, stored);
+    case 64: return dispatch_rp<MODE, 64, NPART>(P, rt, prm, G, st, stored);
     default: return set_error(SENSE_EUNSUPPORTED, "padded coils not in {8,16,32,64}");
   }
 }
 
 int tc_launch(sense_plan_s* P, int mode, int npart, int cp, int rt, const tc::Params& prm, int G,
-              cudaStream_t st) {
+              cudaStream_t st, bool stored) {
   if (mode == tc::ENC)
-    return npart == 2 ? dispatch_cp<tc::ENC, 2>(P, cp, rt, prm, G, st)
-                      : dispatch_cp<tc::ENC, 1>(P, cp, rt, prm, G, st);
-  return npart == 2 ? dispatch_cp<tc::ADJ, 2>(P, cp, rt, prm, G, st)
-                    : dispatch_cp<tc::ADJ, 1>(P, cp, rt, prm, G, st);
+    return npart == 2 ? dispatch_cp<tc::ENC, 2>(P, cp, rt, prm, G, st, stored)
+                      : dispatch_cp<tc::ENC, 1>(P, cp, rt, prm, G, st, stored);
+  return npart == 2 ? dispatch_cp<tc::ADJ, 2>(P, cp, rt, prm, G, st, stored)
+                    : dispatch_cp<tc::ADJ, 1>(P, cp, rt, prm, G, st, stored);
 }
 
 static void tc_free_layout(sense_plan_s* P) {
@@ -965,6 +1010,9 @@ int tc_setup(sense_plan_s* P) {
 
 void tc_free(sense_plan_s* P) {
   tc_free_layout(P);
+  cudaFree(P->p_enc);
+  cudaFree(P->p_adj);
+  P->p_enc = P->p_adj = nullptr;
   cudaFree(P->Qimg); cudaFree(P->Yimg); cudaFree(P->qscale);
   cudaFree(P->yscale); cudaFree(P->colmax); cudaFree(P->tc_err);
 }
@@ -1104,6 +1152,7 @@ static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, co
   d.n_outer = enc ? P->nsb : P->nvb;
   d.n_inner = enc ? P->nvb : P->nsb;
   d.chunk = d.n_inner;
+  d.stored = enc ? P->p_enc : P->p_adj;
   prm.inst = nullptr;
   prm.first_cta = enc ? P->tc_first_e : P->tc_first_a;
   prm.W = (long long)d.n_outer * d.n_inner;
@@ -1111,7 +1160,7 @@ static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, co
   prm.stop = stop;
   prm.seg_len = P->tc_seg_len;
   const int G = P->tc_grid;
-  return tc_launch(P, mode, npart, P->Cp, P->RT, prm, G, st);
+  return tc_launch(P, mode, npart, P->Cp, P->RT, prm, G, st, d.stored != nullptr);
 }
 
 static int npart_of(int prec) { return prec == SENSE_PREC_TC_SPLIT ? 2 : 1; }
@@ -1140,6 +1189,98 @@ int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool c
   return tc_reduce_x(P, P->Xpart_tc, P->tc_nslot_a, q, stop, st);
 }
 
+namespace tc {
+
+// Stored-P mode: the phase tiles of one pass, computed once with exactly the pass kernel's
+// per-element arithmetic (anchor sum, the delta FMAs in row order, range reduction, MUFU
+// sin/cos, FP16 hi/lo split), so a pass that streams them is bit-identical to one that
+// generates them. One CTA of 128 threads (one per row) per (row block, streamed block) pair;
+// chunk c = (stage, warpgroup, half) holds the 8 streamed elements the pass kernel's warpgroup
+// writes to tensor memory at once, for the 4 matrices re hi, re lo, im hi, im lo.
+template <int MODE>
+__global__ void __launch_bounds__(128) gen_stored_kernel(InstDesc d, int RT, long long W,
+                                                         uint4* __restrict__ out) {
+  __shared__ float s_col[MAX_RP * 128];
+  __shared__ float s_anc[128];
+  const int row = threadIdx.x;
+  const float ang_scale = MODE == ADJ ? -6.283185307179586f : 6.283185307179586f;
+  const float RND = 12582912.f;
+  for (long long w = blockIdx.x; w < W; w += gridDim.x) {
+    const int o = (int)(w / d.n_inner), in = (int)(w % d.n_inner);
+    __syncthreads();
+    for (int i = threadIdx.x; i < RT * 128; i += blockDim.x)
+      s_col[i] = d.colT[(long long)in * 128 * RT + i];
+    s_anc[row] = d.colAnc[(long long)o * d.cols_total + (long long)in * 128 + row];
+    __syncthreads();
+    float own[MAX_RP];
+    for (int q = 0; q < RT; ++q) own[q] = d.rowT[((long long)o * RT + q) * 128 + row];
+    const float rb = d.rowAnc[(long long)in * d.rows_total + (long long)o * 128 + row];
+    for (int c = 0; c < 16; ++c) {
+      const int st = c >> 3, g = (c >> 1) & 3, jh = c & 1;
+      const int v0 = st * 64 + g * 16 + jh * 8;
+      uint32_t wv[4][4];
+      for (int k = 0; k < 4; ++k) {
+        float cs[2], sn[2];
+        for (int e = 0; e < 2; ++e) {
+          const int v = v0 + 2 * k + e;
+          float t = __fadd_rn(s_anc[v], rb);
+          for (int q = 0; q < RT; ++q) t = __fmaf_rn(own[q], s_col[q * 128 + v], t);
+          const float tr = __fmaf_rn(__fadd_rn(__fadd_rn(t, RND), -RND), -1.0f, t);
+          const float ang = __fmul_rn(tr, ang_scale);
+          __sincosf(ang, &sn[e], &cs[e]);
+        }
+        const float2 hc = hi11(make_float2(cs[0], cs[1])), hs = hi11(make_float2(sn[0], sn[1]));
+        wv[0][k] = pack_h2(hc.x, hc.y);
+        wv[1][k] = pack_h2(__fmaf_rn(hc.x, -1.0f, cs[0]), __fmaf_rn(hc.y, -1.0f, cs[1]));
+        wv[2][k] = pack_h2(hs.x, hs.y);
+        wv[3][k] = pack_h2(__fmaf_rn(hs.x, -1.0f, sn[0]), __fmaf_rn(hs.y, -1.0f, sn[1]));
+      }
+      uint4* dst = out + ((w * 16 + c) * 4) * 128 + row;
+      for (int m = 0; m < 4; ++m) dst[m * 128] = make_uint4(wv[m][0], wv[m][1], wv[m][2], wv[m][3]);
+    }
+  }
+}
+
+}  // namespace tc
+
+int tc_store_p(sense_plan_s* P, bool enable, cudaStream_t st) {
+  cudaFree(P->p_enc);
+  cudaFree(P->p_adj);
+  P->p_enc = P->p_adj = nullptr;
+  if (!enable) return SENSE_OK;
+  const size_t bytes = (size_t)P->nsb * P->nvb * 16 * 4 * 128 * sizeof(uint4);
+  if (cudaMalloc((void**)&P->p_enc, bytes) != cudaSuccess ||
+      cudaMalloc((void**)&P->p_adj, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(P->p_enc);
+    cudaFree(P->p_adj);
+    P->p_enc = P->p_adj = nullptr;
+    return set_error(SENSE_ENOMEM, "stored phase tiles (" + std::to_string(2 * bytes >> 20) +
+                                       " MiB)");
+  }
+  for (int mode = 0; mode < 2; ++mode) {
+    const bool enc = mode == tc::ENC;
+    tc::InstDesc d = {};
+    d.rowT = enc ? P->dKt : P->dRt;
+    d.colT = enc ? P->dRt : P->dKt;
+    d.rowAnc = enc ? P->Banc : P->Aanc;
+    d.colAnc = enc ? P->Aanc : P->Banc;
+    d.rows_total = enc ? P->Kp : P->Lp;
+    d.cols_total = enc ? P->Lp : P->Kp;
+    d.n_outer = enc ? P->nsb : P->nvb;
+    d.n_inner = enc ? P->nvb : P->nsb;
+    const long long W = (long long)d.n_outer * d.n_inner;
+    const int grid = (int)std::min<long long>(W, 32LL * P->num_sms);
+    if (enc)
+      tc::gen_stored_kernel<tc::ENC><<<grid, 128, 0, st>>>(d, P->RT, W, P->p_enc);
+    else
+      tc::gen_stored_kernel<tc::ADJ><<<grid, 128, 0, st>>>(d, P->RT, W, P->p_adj);
+    SENSE_CUDA_TRY(cudaGetLastError());
+    count_launch(P);
+  }
+  return SENSE_OK;
+}
+
 int tc_check_error(sense_plan_s* P) {
   int e = 0;
   SENSE_CUDA_TRY(cudaMemcpy(&e, P->tc_err, 4, cudaMemcpyDeviceToHost));
@@ -1152,3 +1293,16 @@ int tc_check_error(sense_plan_s* P) {
 }
 
 }  // namespace sense
+
+extern "C" int sense_plan_store_p(sense_plan P, int32_t enable, void* stream) {
+  if (!P) return sense::set_error(SENSE_EINVAL, "null plan");
+  int dev = -1;
+  SENSE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != P->device) return sense::set_error(SENSE_EINVAL, "plan belongs to another device");
+  cudaStream_t st = (cudaStream_t)stream;
+  SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+  const int rc = sense::tc_store_p(P, enable != 0, st);
+  if (rc != SENSE_OK) return rc;
+  SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+  return SENSE_OK;
+}

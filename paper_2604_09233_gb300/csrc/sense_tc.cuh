@@ -21,6 +21,9 @@ struct InstDesc {
   int n_outer, n_inner;
   int chunk;             // work queue: streamed blocks per work item (slot = first / chunk)
   int pad;
+  // stored phase tiles (stored-P mode): per (row block, streamed block) pair 16 chunks
+  // (stage, warpgroup, half) of [4 matrices: re hi, re lo, im hi, im lo][128 rows][8 FP16]
+  const uint4* stored;
 };
 
 // Two schedules feed the same kernel:
@@ -54,9 +57,12 @@ enum Mode { ENC = 0, ADJ = 1 };
 
 }  // namespace tc
 
-// Launch one pass (template chosen by npart, cp = padded coils, rt = delta rows) on G CTAs.
+// Launch one pass (template chosen by npart, cp = padded coils, rt = delta rows) on G CTAs;
+// stored: the phase tiles come from prm's descriptors' `stored` arrays.
 int tc_launch(sense_plan_s* P, int mode, int npart, int cp, int rt, const tc::Params& prm, int G,
-              cudaStream_t st);
+              cudaStream_t st, bool stored = false);
+// Stored-P mode: generate (enable) or free the phase tiles of both passes.
+int tc_store_p(sense_plan_s* P, bool enable, cudaStream_t st);
 // B image of src (Y_int layout, nrows x Cp) or of S o pv; colmax computed unless have_colmax.
 int tc_make_image(sense_plan_s* P, int npart, const float2* src, const float2* pv,
                   long long nrows, unsigned* colmax, float* bscale, uint8_t* img,

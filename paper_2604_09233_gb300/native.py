@@ -33,7 +33,7 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_batch_create", "sense_batch_destroy", "sense_batch_plan", "sense_batch_info",
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
             "sense_batch_autotune", "sense_cg_solve_iterates", "sense_kspace_filter_mask",
-            "sense_kspace_filter"]
+            "sense_kspace_filter", "sense_plan_store_p"]
 
 
 class SenseError(RuntimeError):
@@ -92,6 +92,7 @@ def _load():
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "sense_kspace_filter_mask": ([i32, i32, dbl, dbl, vp, vp, i64, vp], ctypes.c_int),
         "sense_kspace_filter": ([i32, i32, i32, vp, vp, vp], ctypes.c_int),
+        "sense_plan_store_p": ([vp, i32, vp], ctypes.c_int),
         "sense_cg_solve_iterates": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp,
                                      ctypes.POINTER(CGInfo), vp], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
@@ -252,6 +253,11 @@ def sense_cg_solve_iterates(plan, s, iterates, max_iter, prec=SENSE_PREC_FP32, r
            "sense_cg_solve_iterates")
     out = dict(iters=info.iters, status=info.status, rr0=info.rr0, rr_final=info.rr_final)
     return out, hist[: info.iters + 1]
+
+
+def sense_plan_store_p(plan, enable=True, stream=None):
+    """Stored-P mode on (precomputed phase tiles streamed from HBM) or off."""
+    _check(_lib.sense_plan_store_p(plan, 1 if enable else 0, stream), "sense_plan_store_p")
 
 
 def sense_kspace_filter_mask(nx, ny, dx, dy, kx, ky):
