@@ -45,6 +45,10 @@ def _parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true",
                     help="skip the (untimed) differentiation measurements")
+    ap.add_argument("--no-stored", action="store_true",
+                    help="skip the (untimed) stored-P comparison")
+    ap.add_argument("--stored", action="store_true",
+                    help="--op-only: stream stored phase tiles instead of generating them")
     ap.add_argument("--op-only", action="store_true",
                     help="time only W + K single E^H E applies (used for kernel profiling)")
     return ap.parse_args()
@@ -60,6 +64,8 @@ def run_op_only(args):
     wl = _workload(args.workload)
     dev = torch.device("cuda", 0)
     plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
+    if args.stored:
+        native.sense_plan_store_p(plan.handle, True)
     m = torch.from_numpy(wl.m_true.astype(np.complex64)).to(dev)
     out = torch.empty_like(m)
     for _ in range(args.warmup):
@@ -71,6 +77,7 @@ def run_op_only(args):
     torch.cuda.synchronize()
     st = native.sense_plan_stats(plan.handle)
     print(json.dumps({"op_only": True, "workload": wl.name, "precision": prec_name,
+                      "stored": bool(args.stored),
                       "steps": args.steps, "stats": st}), flush=True)
     plan.close()
 
@@ -251,10 +258,12 @@ def run_reference(args):
 # from one ncu capture, profiles/tc_pass_2d256_32coil_sh3.md), keyed by the SHA-256 of the
 # pass-kernel source they were taken on (pass_kernel_source_hash); any other source reports null.
 KERNEL_TRAFFIC = {
-    "cc41474d781cf7698599f881f02bc82b59d59ab57b6a57c98974a18e31b10b03": {
+    "a74297ff0bfa8bfe635035571e66aea0bd8ba6864033d8a0329cc184951824f4": {
         "workload": "2d_256x256_32coil_35750samp_sh3", "precision": "tc_split",
-        "tc_encode_pass": (169.044736 + 9.572608) * 1e6,
-        "tc_adjoint_pass": (182.273280 + 3.996928) * 1e6,
+        "tc_encode_pass": 169214464 + 8960256,
+        "tc_adjoint_pass": 182843392 + 798976,
+        "stored_tc_encode_pass": 19579746816 + 12485376,
+        "stored_tc_adjoint_pass": 19522087424 + 686080,
     },
 }
 
@@ -451,6 +460,40 @@ def run_ours(args):
         kfilter = {"filter_ms": ev[0].elapsed_time(ev[1]) / 3, "mask_host_ms": 1e3 * t_mask,
                    "mask_fraction": float(mask.mean())}
 
+    # ---------------------------------------------------------------- stored P (untimed)
+    # the paper's alternative: phase tiles computed once, streamed from HBM every pass
+    stored = None
+    if not args.no_stored:
+        info_p = plan.info
+        tile_bytes = 16 * info_p["L_padded"] * info_p["K_padded"]       # both passes, hi + lo
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        try:
+            ev[0].record(stream)
+            native.sense_plan_store_p(plan.handle, True)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            t_gen = ev[0].elapsed_time(ev[1])
+            r_split = apply_rate(native.SENSE_PREC_TC_SPLIT, reps=5)
+            r_fp16 = apply_rate(native.SENSE_PREC_TC_FP16, reps=5)
+            x_st = torch.empty_like(x)
+            native.sense_cg_solve(plan.handle, s, x_st, n_it, prec=prec, history=False)
+            torch.cuda.synchronize()
+            same = bool(torch.equal(x_st, x_tc)) if prec == native.SENSE_PREC_TC_SPLIT else None
+            native.sense_plan_store_p(plan.handle, False)
+            # per split apply the two passes read 8 bytes per (sample, voxel) pair each
+            gbs = tile_bytes * r_split / 1e9
+            stored = {"tile_bytes": tile_bytes, "generate_ms": t_gen,
+                      "traffic_per_pass": {k: _kernel_traffic(wl.name, prec_name, "stored_" + k)
+                                           for k in ("tc_encode_pass", "tc_adjoint_pass")},
+                      "applies_per_s": {"tc_split": r_split, "tc_fp16": r_fp16},
+                      "vs_generated": {"tc_split": r_split / rates["tc_split"],
+                                       "tc_fp16": r_fp16 / rates["tc_fp16"]},
+                      "tile_read_gbs_split": gbs,
+                      "frac_of_measured_hbm": gbs / _peaks()[0]["hbm_gbs"],
+                      "cg_bit_identical_to_generated": same}
+        except native.SenseError as e:
+            stored = {"unavailable": str(e)}
+
     # ---------------------------------------------------------------- roofline
     # dominant kernel: the tensor-core pass (E or E^H) with the larger share of event time
     peaks, peak_kind = _peaks()
@@ -499,6 +542,8 @@ def run_ours(args):
         line["differentiation"] = diff
     if kfilter is not None:
         line["kspace_filter"] = kfilter
+    if stored is not None:
+        line["stored_p"] = stored
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_apply_rate(wl)
         cb.pop("seconds")
