@@ -123,11 +123,40 @@ extern "C" int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, doubl
   const std::vector<Pt> h = convex_hull(pts);
   // boundary tolerance: a tiny fraction of the grid's k-space spacing
   const double eps = 1e-9 * 2.0 * M_PI / std::max(nx * dx, ny * dy);
-  for (int v = 0; v < ny; ++v)
-    for (int u = 0; u < nx; ++u) {
-      const Pt q = {2.0 * M_PI * (u - nx / 2) / (nx * dx), 2.0 * M_PI * (v - ny / 2) / (ny * dy)};
-      mask[(size_t)v * nx + u] = inside(h, q, eps) ? 1.0f : 0.0f;
+  const double dkx = 2.0 * M_PI / (nx * dx), dky = 2.0 * M_PI / (ny * dy);
+  std::fill(mask, mask + (size_t)nx * ny, 0.0f);
+  if (h.size() < 3) return SENSE_OK;
+  for (int v = 0; v < ny; ++v) {
+    // a convex polygon cuts a horizontal line in one interval: bound it from the edges that
+    // cross the line, then confirm the candidate points with the exact half-plane test
+    const double y = dky * (v - ny / 2);
+    double lo = INFINITY, hi = -INFINITY;
+    for (size_t i = 0; i < h.size(); ++i) {
+      const Pt& a = h[i];
+      const Pt& b = h[(i + 1) % h.size()];
+      if ((y < std::min(a.y, b.y) - eps) || (y > std::max(a.y, b.y) + eps)) continue;
+      double xa, xb;
+      if (std::fabs(b.y - a.y) <= eps) {
+        xa = std::min(a.x, b.x);
+        xb = std::max(a.x, b.x);
+      } else {
+        const double s = std::min(1.0, std::max(0.0, (y - a.y) / (b.y - a.y)));
+        xa = xb = a.x + s * (b.x - a.x);
+      }
+      lo = std::min(lo, xa);
+      hi = std::max(hi, xb);
     }
+    if (!(lo <= hi)) continue;
+    const int u0 = std::max(0, (int)std::floor(lo / dkx) + nx / 2 - 1);
+    const int u1 = std::min(nx - 1, (int)std::ceil(hi / dkx) + nx / 2 + 1);
+    // strictly inside the interval (by more than a grid step) is inside the polygon; only the
+    // points near its ends take the exact test
+    for (int u = u0; u <= u1; ++u) {
+      const double x = dkx * (u - nx / 2);
+      const bool sure = x > lo + dkx && x < hi - dkx;
+      if (sure || inside(h, {x, y}, eps)) mask[(size_t)v * nx + u] = 1.0f;
+    }
+  }
   return SENSE_OK;
 }
 

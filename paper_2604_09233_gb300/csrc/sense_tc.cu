@@ -1,4 +1,5 @@
-// Tensor-core (tcgen05) E and E^H with the encoding matrix generated on the fly.
+// Tensor-core (tcgen05) E and E^H with the encoding matrix generated on the fly (or, in the
+// stored-P comparison mode, streamed from HBM).
 //
 // One kernel template serves both passes. A pass contracts the phase matrix P = e^{i K R}
 // (Eq. 4) against a thin complex operand over one of its two dimensions:
@@ -12,13 +13,18 @@
 //   1 MMA warp          : issues tcgen05.mma (A from TMEM, B from shared memory) into two
 //                         FP32 accumulators D1 = A_re B^T, D2 = A_im B^T;
 //   1 loader warp       : bulk-copies (cp.async.bulk) the B tile image, the streamed
-//                         block's phase deltas and its anchors into shared memory.
+//                         block's phase deltas and its anchors into shared memory, and
+//                         publishes each stage's (instance, row block, streamed block, run
+//                         flags, output slot) in a shared-memory metadata ring.
 // B is the real [2C][64] matrix [B_re; B_im] (per-coil power-of-two scaled FP16, prepared
 // as a pre-swizzled 128B-K-major image), so D1 and D2 give the complex product:
 //   Y_re = D1[:, c] - D2[:, C+c],  Y_im = D1[:, C+c] + D2[:, c].
-// Work is split stream-K: the (row block, streamed block) pairs are cut into equal
-// contiguous ranges, one per CTA; a run of pairs with the same row block accumulates in
-// TMEM and is written to a partial slot, summed in a fixed order afterwards.
+// The loader's schedule is stream-K for one problem (the (row block, streamed block) pairs
+// cut into equal contiguous ranges, one per CTA; a run of pairs with the same row block
+// accumulates in TMEM and is written to a partial slot, summed in a fixed order afterwards)
+// or, for a batch, an atomic work queue of (instance, row block, chunk) items. In the STORED
+// variant the generator warps copy precomputed phase tiles from HBM into tensor memory
+// instead of computing them (gen_stored_kernel writes those tiles once).
 // Every wait is bounded: on time-out the CTA records an error, drains what it issued,
 // frees its tensor memory and returns.
 #include <cuda_fp16.h>
