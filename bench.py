@@ -258,7 +258,7 @@ def run_reference(args):
 # from one ncu capture, profiles/tc_pass_2d256_32coil_sh3.md), keyed by the SHA-256 of the
 # pass-kernel source they were taken on (pass_kernel_source_hash); any other source reports null.
 KERNEL_TRAFFIC = {
-    "a74297ff0bfa8bfe635035571e66aea0bd8ba6864033d8a0329cc184951824f4": {
+    "3faf7cb8a46440bd0d3c1642430adbae4341ce8bc1237890b183e9490b8e8fdf": {
         "workload": "2d_256x256_32coil_35750samp_sh3", "precision": "tc_split",
         "tc_encode_pass": 169214464 + 8960256,
         "tc_adjoint_pass": 182843392 + 798976,
@@ -269,16 +269,23 @@ KERNEL_TRAFFIC = {
 
 
 def pass_kernel_source_hash():
-    """SHA-256 of the pass kernel's source: sense_tc.cu up to the end of tc_pass_kernel (its
-    helpers and the kernel itself) followed by sense_tc.cuh."""
+    """SHA-256 of the pass kernel's code: sense_tc.cu up to the end of tc_pass_kernel (its
+    helpers and the kernel itself) followed by sense_tc.cuh, with // comments and blank lines
+    removed (they do not change the compiled kernel)."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_2604_09233_gb300", "csrc")
-    with open(os.path.join(csrc, "sense_tc.cu"), "rb") as fh:
+
+    def code(text):
+        lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+        return "\n".join(ln for ln in lines if ln.strip()).encode()
+
+    with open(os.path.join(csrc, "sense_tc.cu")) as fh:
         text = fh.read()
-    end = text.index(b"template <int CP, int RP, int NPART>\nconstexpr size_t smem_bytes()")
-    h = hashlib.sha256(text[:end])
-    with open(os.path.join(csrc, "sense_tc.cuh"), "rb") as fh:
-        h.update(fh.read())
+    end = text.index("template <int CP, int RP, int NPART>\nconstexpr size_t smem_bytes()")
+    h = hashlib.sha256(code(text[:end]))
+    with open(os.path.join(csrc, "sense_tc.cuh")) as fh:
+        h.update(code(fh.read()))
     return h.hexdigest()
 
 
