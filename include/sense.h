@@ -234,6 +234,34 @@ int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, double dy, const
 int sense_kspace_filter(int32_t nx, int32_t ny, int32_t nz, const float* mask, float* image,
                         void* stream);
 
+/* Map smoothing and extrapolation (Eq. 1: sensitivity maps; Eq. 3: the B0 map) -------------
+ * Solves, on an nx x ny x nz grid (raster order, x fastest), the least-squares system of the
+ * two equations, A x = [w0 o xhat; 0; 0; 0] with A = [diag(w0); sqrt(alpha) diag(wd) D_x;
+ * sqrt(alpha) diag(wd) D_y; sqrt(alpha) diag(wd) D_z], D the second difference (order 2, Eq. 1:
+ * w0 = trusted mask M_T, wd = reconstruction mask M_R) or the first difference (order 1, Eq. 3:
+ * w0 = 1, wd = the standard error of the phase fit), through its normal equations by CG from
+ * x = xhat. Second-difference rows exist at interior voxels, first-difference rows where the
+ * next voxel exists; a row is weighted by wd at its voxel; axes of length 1 have none.
+ * w0, wd [n] float, xhat, x [n] complex64 (real maps: zero imaginary parts), DEVICE memory;
+ * x may equal xhat. Voxels that no equation constrains (w0 = 0 and no weighted derivative row
+ * touches them) keep xhat. info (nullable): iterations run and the final relative residual of the
+ * normal equations. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t order;      /* 1 or 2                                                         */
+  double alpha;       /* smoothness weight (alpha_B or alpha_S)                         */
+  int32_t max_iter;
+  double rel_tol;     /* stop when ||r|| <= rel_tol ||diag(w0^2) xhat||                 */
+} sense_smooth_opts;
+
+typedef struct {
+  int32_t iters;
+  double rel_residual;
+} sense_smooth_info;
+
+int sense_smooth_map(const sense_smooth_opts* opts, const float* w0, const float* wd,
+                     const float* xhat, float* x, sense_smooth_info* info, void* stream);
+
 /* Batched reconstruction -----------------------------------------------------------------
  * (no counterpart in the paper, which reconstructs one slice or volume at a time)
  * A batch holds n independent problems of uneven size (voxels, samples, coils, basis rows)

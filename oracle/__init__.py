@@ -12,6 +12,8 @@ Functions and the passages they follow:
   cg           Fig. 2 Alg. 1 steps 3-18
   grad_omega   chain rule of Eq. 4 w.r.t. row 0 of R (the B0 map)
   grad_omega_adjoint  chain rule of Eq. 5 w.r.t. row 0 of R (backward of x = E^H y)
+  smooth_map   Eqs. 1 and 3: smoothing and extrapolation of sensitivity / B0 maps as a sparse
+               least-squares problem, solved directly
   kspace_mask  the k-space filter: Cartesian points inside the Delaunay triangulation of the
                first-order k-space coordinates (k-space filter section)
   kspace_filter  rho <- IFFT(FFT(rho) o f), Fig. 2 Alg. 1 step 19, as dense transforms
@@ -33,6 +35,7 @@ from .oracle import (  # noqa: F401
     grad_omega_adjoint,
     kspace_mask,
     kspace_filter,
+    smooth_map,
     lcurve_corner,
     num_threads,
     set_num_threads,

@@ -171,6 +171,55 @@ def grad_omega_adjoint(Kmat, Rmat, S, y, h, j=None):
     return out
 
 
+def smooth_map(shape, order, alpha, w0, wd, xhat):
+    """Least-squares solution of Eq. 1 (order 2, second differences; w0 = M_T, wd = M_R) or
+    Eq. 3 (order 1, first differences; w0 = 1, wd = the fit's standard error):
+    A x = [w0 o xhat; 0; 0; 0], A = [diag(w0); sqrt(alpha) diag(wd) D_x; ... D_y; ... D_z],
+    with the sparse A written out row by row (second-difference rows at interior voxels, first-
+    difference rows where the next voxel exists, weight wd at the row's voxel) and the normal
+    equations solved directly; voxels that no equation constrains keep xhat. shape: (ny, nx)
+    or (nz, ny, nx); x fastest."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    shape = tuple(shape)
+    n = int(np.prod(shape))
+    idx = np.arange(n).reshape(shape)
+    w0 = np.asarray(w0, float).ravel()
+    wd = np.asarray(wd, float).ravel()
+    blocks = [sp.diags(w0)]
+    for ax in range(len(shape)):
+        m = shape[ax]
+        if m < 2:
+            continue
+        rows, cols, vals = [], [], []
+        sl = np.moveaxis(idx, ax, -1).reshape(-1, m)
+        r = 0
+        for line in sl:
+            if order == 1:
+                for c in range(m - 1):
+                    rows += [r, r]
+                    cols += [line[c], line[c + 1]]
+                    vals += [-wd[line[c]], wd[line[c]]]
+                    r += 1
+            else:
+                for c in range(1, m - 1):
+                    rows += [r, r, r]
+                    cols += [line[c - 1], line[c], line[c + 1]]
+                    vals += [wd[line[c]], -2 * wd[line[c]], wd[line[c]]]
+                    r += 1
+        blocks.append(np.sqrt(alpha) * sp.csr_matrix((vals, (rows, cols)), shape=(r, n)))
+    A = sp.vstack(blocks).tocsc()
+    rhs = np.concatenate([w0 * np.asarray(xhat, complex).ravel(),
+                          np.zeros(A.shape[0] - n, complex)])
+    N = (A.T @ A).tocsc()
+    # voxels that no equation constrains (outside the data and derivative weights) keep xhat
+    x = np.asarray(xhat, complex).ravel().copy()
+    keep = N.diagonal() > 0
+    if keep.any():
+        x[keep] = spl.spsolve(N[keep][:, keep].tocsc(), (A.T @ rhs)[keep])
+    return x
+
+
 def kspace_mask(nx, ny, dx, dy, kx, ky):
     """k-space filter of the paper's k-space filter section: 1 for the Cartesian k-space
     points 2 pi (u - n/2) / (n d) that lie in a triangle of the Delaunay triangulation of the

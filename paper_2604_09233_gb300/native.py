@@ -33,7 +33,7 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_batch_create", "sense_batch_destroy", "sense_batch_plan", "sense_batch_info",
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
             "sense_batch_autotune", "sense_cg_solve_iterates", "sense_kspace_filter_mask",
-            "sense_kspace_filter", "sense_plan_store_p"]
+            "sense_kspace_filter", "sense_plan_store_p", "sense_smooth_map"]
 
 
 class SenseError(RuntimeError):
@@ -69,6 +69,16 @@ class CGOpts(ctypes.Structure):
                 ("apply_j", ctypes.c_int32)]
 
 
+class SmoothOpts(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double)]
+
+
+class SmoothInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+
 class CGInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rr0", ctypes.c_double), ("rr_final", ctypes.c_double)]
@@ -93,6 +103,8 @@ def _load():
         "sense_kspace_filter_mask": ([i32, i32, dbl, dbl, vp, vp, i64, vp], ctypes.c_int),
         "sense_kspace_filter": ([i32, i32, i32, vp, vp, vp], ctypes.c_int),
         "sense_plan_store_p": ([vp, i32, vp], ctypes.c_int),
+        "sense_smooth_map": ([ctypes.POINTER(SmoothOpts), vp, vp, vp, vp,
+                              ctypes.POINTER(SmoothInfo), vp], ctypes.c_int),
         "sense_cg_solve_iterates": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp,
                                      ctypes.POINTER(CGInfo), vp], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
@@ -258,6 +270,23 @@ def sense_cg_solve_iterates(plan, s, iterates, max_iter, prec=SENSE_PREC_FP32, r
 def sense_plan_store_p(plan, enable=True, stream=None):
     """Stored-P mode on (precomputed phase tiles streamed from HBM) or off."""
     _check(_lib.sense_plan_store_p(plan, 1 if enable else 0, stream), "sense_plan_store_p")
+
+
+def sense_smooth_map(shape, order, alpha, w0, wd, xhat, x, max_iter=2000, rel_tol=1e-7,
+                     stream=None):
+    """Eq. 1 (order 2) / Eq. 3 (order 1) smoothing on a grid of `shape` ((ny, nx) or
+    (nz, ny, nx)); w0, wd float32 and xhat, x complex64 CUDA tensors. Returns the info dict."""
+    nz, ny, nx = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
+    o = SmoothOpts(int(nx), int(ny), int(nz), int(order), float(alpha), int(max_iter),
+                   float(rel_tol))
+    info = SmoothInfo()
+    p0, _, s0 = _ptr(w0, np.float32)
+    p1, _, _ = _ptr(wd, np.float32)
+    p2, _, _ = _ptr(xhat)
+    p3, _, _ = _ptr(x)
+    _check(_lib.sense_smooth_map(ctypes.byref(o), p0, p1, p2, p3, ctypes.byref(info),
+                                 _stream(s0, explicit=stream)), "sense_smooth_map")
+    return {"iters": info.iters, "rel_residual": info.rel_residual}
 
 
 def sense_kspace_filter_mask(nx, ny, dx, dy, kx, ky):

@@ -287,3 +287,41 @@ def test_kspace_mask_of_a_square_of_samples():
     expect = np.zeros((ny, nx))
     expect[4 - 1: 4 + 2, 4 - 2: 4 + 3] = 1.0
     assert np.array_equal(m, expect)
+
+
+def test_smooth_map_pins():
+    """Eq. 1 / Eq. 3 smoothing: a field in the null space of the derivative is returned unchanged
+    for any alpha (linear for second differences, constant for first differences); with the
+    data term on half the grid only (Eq. 1 with M_T a half, M_R everything) a linear field is
+    continued exactly over the other half; alpha = 0 returns the data where w0 = 1; and the
+    normal equations hold for a random field."""
+    ny, nx = 7, 9
+    y, x = np.mgrid[:ny, :nx]
+    lin = (0.3 + 0.2j) * x - (0.1 - 0.4j) * y + 1.0
+    ones = np.ones((ny, nx))
+    assert np.allclose(oracle.smooth_map((ny, nx), 2, 5.0, ones, ones, lin), lin.ravel())
+    const = np.full((ny, nx), 2.0 - 1.0j)
+    rng = np.random.default_rng(7)
+    eps = rng.uniform(0.5, 2.0, size=(ny, nx))
+    assert np.allclose(oracle.smooth_map((ny, nx), 1, 3.0, ones, eps, const), const.ravel())
+    half = (x < nx // 2).astype(float)
+    garbage = np.where(half > 0, lin, 50.0 + 7j)            # data outside M_T is ignored
+    assert np.allclose(oracle.smooth_map((ny, nx), 2, 0.7, half, ones, garbage), lin.ravel())
+    z = rng.normal(size=(ny, nx)) + 1j * rng.normal(size=(ny, nx))
+    assert np.allclose(oracle.smooth_map((ny, nx), 1, 0.0, ones, eps, z), z.ravel())
+    # 3D: a linear field along all three axes is kept by second differences
+    zz, yy, xx = np.mgrid[:4, :5, :6]
+    lin3 = 1.0 + 0.5 * xx - 0.25 * yy + 0.125j * zz
+    o3 = np.ones((4, 5, 6))
+    assert np.allclose(oracle.smooth_map((4, 5, 6), 2, 2.0, o3, o3, lin3), lin3.ravel())
+
+
+def test_smooth_map_weight_sits_on_the_row_voxel():
+    """Three voxels, first differences (Eq. 3), alpha = 1, weights (1, 2, 5): the rows are
+    w_0 (x1 - x0) and w_1 (x2 - x1) (the last voxel has no row, its weight is unused), so the
+    normal matrix is I + [[1, -1, 0], [-1, 1 + 4, -4], [0, -4, 4]]."""
+    N = np.eye(3) + np.array([[1.0, -1.0, 0.0], [-1.0, 5.0, -4.0], [0.0, -4.0, 4.0]])
+    xhat = np.array([1.0, -2.0, 0.5j])
+    expect = np.linalg.solve(N, xhat)
+    got = oracle.smooth_map((1, 3), 1, 1.0, np.ones(3), np.array([1.0, 2.0, 5.0]), xhat)
+    assert np.allclose(got, expect)
