@@ -222,7 +222,7 @@ int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const doub
  * sense_kspace_filter_mask (host only): f for an nx x ny grid of spacing dx, dy (m): 1 for the
  *   Cartesian k-space points k = 2 pi (u - n/2) / (n d) inside (or on) the convex hull of the
  *   K first-order coefficients (kx, ky) (rad/m) of the samples, else 0; mask [ny][nx] host
- *   float. 2D only (a 3D hull is not implemented). Errors: EINVAL, ENONFINITE.
+ *   float. Errors: EINVAL, ENONFINITE.
  * sense_kspace_filter: image [nz][ny][nx] complex64 (DEVICE, raster order = the user voxel
  *   order of a full-grid problem) filtered in place with mask [nz][ny][nx] float (DEVICE),
  *   using the signal model's sign: F(k_u) = sum_x rho(x) e^{+i k_u r_x}, r_x = (x - n/2) d,
@@ -231,6 +231,13 @@ int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const doub
  *   Errors: EINVAL, ENOMEM, ECUDA. */
 int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, double dy, const double* kx,
                              const double* ky, int64_t K, float* mask);
+/* 3D: the same for an nx x ny x nz grid (mask [nz][ny][nx]) and samples (kx, ky, kz) that lie on
+ * at most 4096 kz planes (stacks of planar trajectories): the hull's cross-section at each grid
+ * kz is the 2D convex hull of (1 - t) H_i + t H_j over the plane pairs bracketing it (H_i the 2D
+ * hull of plane i), so only 2D geometry is needed. Errors: EINVAL, ENONFINITE, EUNSUPPORTED. */
+int sense_kspace_filter_mask3d(int32_t nx, int32_t ny, int32_t nz, double dx, double dy,
+                               double dz, const double* kx, const double* ky, const double* kz,
+                               int64_t K, float* mask);
 int sense_kspace_filter(int32_t nx, int32_t ny, int32_t nz, const float* mask, float* image,
                         void* stream);
 

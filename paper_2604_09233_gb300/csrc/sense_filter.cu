@@ -104,31 +104,13 @@ bool inside(const std::vector<Pt>& h, const Pt& q, double eps) {
   return true;
 }
 
-}  // namespace
-}  // namespace sense
-
-using namespace sense;
-
-extern "C" int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, double dy,
-                                        const double* kx, const double* ky, int64_t K,
-                                        float* mask) {
-  if (nx < 1 || ny < 1 || !(dx > 0.0) || !(dy > 0.0) || !kx || !ky || K < 3 || !mask)
-    return set_error(SENSE_EINVAL, "sizes, spacings, k-space coordinates (K >= 3) and mask");
-  std::vector<Pt> pts((size_t)K);
-  for (int64_t i = 0; i < K; ++i) {
-    if (!std::isfinite(kx[i]) || !std::isfinite(ky[i]))
-      return set_error(SENSE_ENONFINITE, "non-finite k-space coordinate");
-    pts[i] = {kx[i], ky[i]};
-  }
-  const std::vector<Pt> h = convex_hull(pts);
-  // boundary tolerance: a tiny fraction of the grid's k-space spacing
-  const double eps = 1e-9 * 2.0 * M_PI / std::max(nx * dx, ny * dy);
-  const double dkx = 2.0 * M_PI / (nx * dx), dky = 2.0 * M_PI / (ny * dy);
-  std::fill(mask, mask + (size_t)nx * ny, 0.0f);
-  if (h.size() < 3) return SENSE_OK;
+// Cartesian points (u, v) with k = (dkx (u - nx/2), dky (v - ny/2)) inside or on the convex
+// CCW polygon h: per row, the polygon's interval on that row, the exact half-plane test only
+// near its ends.
+void raster_polygon(const std::vector<Pt>& h, int nx, int ny, double dkx, double dky, double eps,
+                    float* mask) {
+  if (h.size() < 3) return;
   for (int v = 0; v < ny; ++v) {
-    // a convex polygon cuts a horizontal line in one interval: bound it from the edges that
-    // cross the line, then confirm the candidate points with the exact half-plane test
     const double y = dky * (v - ny / 2);
     double lo = INFINITY, hi = -INFINITY;
     for (size_t i = 0; i < h.size(); ++i) {
@@ -149,14 +131,125 @@ extern "C" int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, doubl
     if (!(lo <= hi)) continue;
     const int u0 = std::max(0, (int)std::floor(lo / dkx) + nx / 2 - 1);
     const int u1 = std::min(nx - 1, (int)std::ceil(hi / dkx) + nx / 2 + 1);
-    // strictly inside the interval (by more than a grid step) is inside the polygon; only the
-    // points near its ends take the exact test
     for (int u = u0; u <= u1; ++u) {
       const double x = dkx * (u - nx / 2);
       const bool sure = x > lo + dkx && x < hi - dkx;
       if (sure || inside(h, {x, y}, eps)) mask[(size_t)v * nx + u] = 1.0f;
     }
   }
+}
+
+// Minkowski sum of two convex CCW polygons (each scaled): merge their edges by angle
+std::vector<Pt> minkowski(const std::vector<Pt>& P, double sp, const std::vector<Pt>& Q,
+                          double sq) {
+  std::vector<Pt> out;
+  if (P.empty() || Q.empty()) return out;
+  if (P.size() < 3 || Q.size() < 3) {        // degenerate: all vertex sums
+    for (const Pt& a : P)
+      for (const Pt& b : Q) out.push_back({sp * a.x + sq * b.x, sp * a.y + sq * b.y});
+    return convex_hull(out);
+  }
+  auto start = [](const std::vector<Pt>& H) {
+    size_t k = 0;
+    for (size_t i = 1; i < H.size(); ++i)
+      if (H[i].y < H[k].y || (H[i].y == H[k].y && H[i].x < H[k].x)) k = i;
+    return k;
+  };
+  const size_t i0 = start(P), j0 = start(Q), n = P.size(), m = Q.size();
+  size_t i = 0, j = 0;
+  while (i < n || j < m) {
+    const Pt& a = P[(i0 + i) % n];
+    const Pt& b = Q[(j0 + j) % m];
+    out.push_back({sp * a.x + sq * b.x, sp * a.y + sq * b.y});
+    const Pt& a1 = P[(i0 + i + 1) % n];
+    const Pt& b1 = Q[(j0 + j + 1) % m];
+    const Pt ea = {sp * (a1.x - a.x), sp * (a1.y - a.y)};
+    const Pt eb = {sq * (b1.x - b.x), sq * (b1.y - b.y)};
+    const double c = ea.x * eb.y - ea.y * eb.x;
+    if (j >= m || (i < n && c > 0)) ++i;
+    else if (i >= n || c < 0) ++j;
+    else { ++i; ++j; }
+  }
+  return convex_hull(out);
+}
+
+}  // namespace
+}  // namespace sense
+
+using namespace sense;
+
+extern "C" int sense_kspace_filter_mask3d(int32_t nx, int32_t ny, int32_t nz, double dx, double dy,
+                                          double dz, const double* kx, const double* ky,
+                                          const double* kz, int64_t K, float* mask) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0) || !(dy > 0.0) || !(dz > 0.0) || !kx || !ky ||
+      !kz || K < 4 || !mask)
+    return set_error(SENSE_EINVAL, "sizes, spacings, k-space coordinates (K >= 4) and mask");
+  // group the samples by kz plane (stacks of planar trajectories)
+  std::vector<std::pair<double, std::vector<Pt>>> planes;
+  {
+    std::vector<int64_t> order((size_t)K);
+    for (int64_t i = 0; i < K; ++i) {
+      if (!std::isfinite(kx[i]) || !std::isfinite(ky[i]) || !std::isfinite(kz[i]))
+        return set_error(SENSE_ENONFINITE, "non-finite k-space coordinate");
+      order[i] = i;
+    }
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return kz[a] < kz[b]; });
+    for (int64_t i : order) {
+      if (planes.empty() || kz[i] != planes.back().first) {
+        if (planes.size() >= 4096)
+          return set_error(SENSE_EUNSUPPORTED, "3D mask: more than 4096 distinct kz planes");
+        planes.push_back({kz[i], {}});
+      }
+      planes.back().second.push_back({kx[i], ky[i]});
+    }
+  }
+  for (auto& pl : planes) pl.second = convex_hull(pl.second);
+  const double dkx = 2.0 * M_PI / (nx * dx), dky = 2.0 * M_PI / (ny * dy),
+               dkz = 2.0 * M_PI / (nz * dz);
+  const double eps = 1e-9 * std::max(dkx, dky);
+  const double ztol = 1e-9 * dkz;
+  std::fill(mask, mask + (size_t)nx * ny * nz, 0.0f);
+  // cross-section of the hull at height c: the convex hull of (1 - t) H_i + t H_j over all
+  // plane pairs z_i <= c <= z_j (t = (c - z_i) / (z_j - z_i)), and of H_i for z_i = c
+  for (int w = 0; w < nz; ++w) {
+    const double c = dkz * (w - nz / 2);
+    std::vector<Pt> pts;
+    for (size_t i = 0; i < planes.size(); ++i) {
+      const double zi = planes[i].first;
+      if (std::fabs(zi - c) <= ztol)
+        pts.insert(pts.end(), planes[i].second.begin(), planes[i].second.end());
+      if (zi > c) continue;
+      for (size_t j = i + 1; j < planes.size(); ++j) {
+        const double zj = planes[j].first;
+        if (zj < c || zj - zi <= ztol) continue;
+        const double tt = (c - zi) / (zj - zi);
+        const std::vector<Pt> s = minkowski(planes[i].second, 1.0 - tt, planes[j].second, tt);
+        pts.insert(pts.end(), s.begin(), s.end());
+      }
+    }
+    if (pts.size() < 3) continue;
+    raster_polygon(convex_hull(pts), nx, ny, dkx, dky, eps, mask + (size_t)w * nx * ny);
+  }
+  return SENSE_OK;
+}
+
+extern "C" int sense_kspace_filter_mask(int32_t nx, int32_t ny, double dx, double dy,
+                                        const double* kx, const double* ky, int64_t K,
+                                        float* mask) {
+  if (nx < 1 || ny < 1 || !(dx > 0.0) || !(dy > 0.0) || !kx || !ky || K < 3 || !mask)
+    return set_error(SENSE_EINVAL, "sizes, spacings, k-space coordinates (K >= 3) and mask");
+  std::vector<Pt> pts((size_t)K);
+  for (int64_t i = 0; i < K; ++i) {
+    if (!std::isfinite(kx[i]) || !std::isfinite(ky[i]))
+      return set_error(SENSE_ENONFINITE, "non-finite k-space coordinate");
+    pts[i] = {kx[i], ky[i]};
+  }
+  const std::vector<Pt> h = convex_hull(pts);
+  // boundary tolerance: a tiny fraction of the grid's k-space spacing
+  const double eps = 1e-9 * 2.0 * M_PI / std::max(nx * dx, ny * dy);
+  const double dkx = 2.0 * M_PI / (nx * dx), dky = 2.0 * M_PI / (ny * dy);
+  std::fill(mask, mask + (size_t)nx * ny, 0.0f);
+  raster_polygon(h, nx, ny, dkx, dky, eps, mask);
   return SENSE_OK;
 }
 

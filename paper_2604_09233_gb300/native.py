@@ -33,7 +33,8 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_batch_create", "sense_batch_destroy", "sense_batch_plan", "sense_batch_info",
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
             "sense_batch_autotune", "sense_cg_solve_iterates", "sense_kspace_filter_mask",
-            "sense_kspace_filter", "sense_plan_store_p", "sense_smooth_map"]
+            "sense_kspace_filter", "sense_plan_store_p", "sense_smooth_map",
+            "sense_kspace_filter_mask3d"]
 
 
 class SenseError(RuntimeError):
@@ -102,6 +103,8 @@ def _load():
         "sense_lcurve_corner": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "sense_kspace_filter_mask": ([i32, i32, dbl, dbl, vp, vp, i64, vp], ctypes.c_int),
         "sense_kspace_filter": ([i32, i32, i32, vp, vp, vp], ctypes.c_int),
+        "sense_kspace_filter_mask3d": ([i32, i32, i32, dbl, dbl, dbl, vp, vp, vp, i64, vp],
+                                       ctypes.c_int),
         "sense_plan_store_p": ([vp, i32, vp], ctypes.c_int),
         "sense_smooth_map": ([ctypes.POINTER(SmoothOpts), vp, vp, vp, vp,
                               ctypes.POINTER(SmoothInfo), vp], ctypes.c_int),
@@ -299,6 +302,20 @@ def sense_kspace_filter_mask(nx, ny, dx, dy, kx, ky):
     _check(_lib.sense_kspace_filter_mask(int(nx), int(ny), float(dx), float(dy), kx.ctypes.data,
                                          ky.ctypes.data, int(kx.size), mask.ctypes.data),
            "sense_kspace_filter_mask")
+    return mask
+
+
+def sense_kspace_filter_mask3d(nx, ny, nz, dx, dy, dz, kx, ky, kz):
+    """Convex-hull k-space filter [nz][ny][nx] (float32 numpy) for a stack of planar
+    trajectories."""
+    k = [np.ascontiguousarray(a, np.float64) for a in (kx, ky, kz)]
+    if not (k[0].shape == k[1].shape == k[2].shape):
+        raise ValueError("kx, ky, kz differ in shape")
+    mask = np.empty((int(nz), int(ny), int(nx)), np.float32)
+    _check(_lib.sense_kspace_filter_mask3d(int(nx), int(ny), int(nz), float(dx), float(dy),
+                                           float(dz), k[0].ctypes.data, k[1].ctypes.data,
+                                           k[2].ctypes.data, int(k[0].size), mask.ctypes.data),
+           "sense_kspace_filter_mask3d")
     return mask
 
 
