@@ -445,7 +445,7 @@ def run_ours(args):
                 "finite": bool(torch.isfinite(wbar).all().item() and torch.isfinite(sbar).all().item())}
 
     # ---------------------------------------------------------------- k-space filter (untimed)
-    # Fig. 2 Alg. 1 step 19 on the reconstructed image (2D workloads): convex-hull mask of the
+    # the k-space filtering that ends Alg. 1 (Fig. 2), on the reconstructed image (2D workloads): convex-hull mask of the
     # first-order coefficients (host, once) and the filter (device)
     kfilter = None
     if len(wl.shape) == 2:

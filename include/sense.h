@@ -7,7 +7,7 @@
  *
  *   Eq. 4     P = e^{o i K R},  E m == P (S o (m 1^T))           (s = E m, [K][C])
  *   Eq. 5     E^H sigma == (S* o (P^H Sigma)) 1                   (m = E^H s, [L])
- *   Fig. 2, Alg. 1 steps 1-18: S <- S o j, CG on E^H E rho = E^H sigma from rho = 0,
+ *   Fig. 2, Alg. 1: S <- S o j, CG on E^H E rho = E^H sigma from rho = 0,
  *             rho <- rho o j.
  *
  * Notation (variable table of Fig. 2): L voxels, K samples, C (Gamma) coils, P1 = P + 1
@@ -108,7 +108,7 @@ int sense_encode(sense_plan plan, int prec, const float* m, float* s, void* stre
 /* m = E^H s (Eq. 5). s: [K][C] complex64, m: [L] complex64. */
 int sense_adjoint(sense_plan plan, int prec, const float* s, float* m, void* stream);
 
-/* out = E^H E m (Fig. 2 Alg. 1 step 8). m, out: [L] complex64; may alias. */
+/* out = E^H E m (the normal operator of Alg. 1, Fig. 2). m, out: [L] complex64; may alias. */
 int sense_normal_op(sense_plan plan, int prec, const float* m, float* out, void* stream);
 
 /* CG options. Stopping: the paper's fixed iteration count N_It (max_iter), optionally
@@ -120,7 +120,7 @@ typedef struct {
   int32_t refine_every; /* tensor-core modes: replace the recursive residual by
                            b - E^H E x with the FP32 operator every this many
                            iterations (0 = never)                                      */
-  int32_t apply_j;      /* nonzero: multiply the result by j (Alg. 1 step 18)          */
+  int32_t apply_j;      /* nonzero: multiply the result by j (as Alg. 1 ends)          */
 } sense_cg_opts;
 
 typedef struct {
@@ -130,7 +130,7 @@ typedef struct {
   double rr_final;      /* r_n^H r_n at exit                                           */
 } sense_cg_info;
 
-/* rho = CG(E^H E, E^H s) (Fig. 2 Alg. 1 steps 3-18), starting from rho = 0.
+/* rho = CG(E^H E, E^H s) (the CG loop of Alg. 1, Fig. 2), starting from rho = 0.
  *   s        [K][C] complex64 coil data Sigma (device or host)
  *   x        [L] complex64 output rho (device or host)
  *   history  NULL or HOST double[(max_iter+1)*3]: for n = 0..iters the row
@@ -218,7 +218,7 @@ int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const doub
                          const double* Rmat, const float* S, const float* j, const float* m,
                          float* s, void* stream);
 
-/* k-space filter (Fig. 2 Alg. 1 step 19: rho = IFFT(FFT(rho) o f)) -------------------------
+/* k-space filter (the filtering that ends Alg. 1, Fig. 2: rho = IFFT(FFT(rho) o f)) ---------
  * sense_kspace_filter_mask (host only): f for an nx x ny grid of spacing dx, dy (m): 1 for the
  *   Cartesian k-space points k = 2 pi (u - n/2) / (n d) inside (or on) the convex hull of the
  *   K first-order coefficients (kx, ky) (rad/m) of the samples, else 0; mask [ny][nx] host

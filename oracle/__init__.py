@@ -6,17 +6,18 @@ shares no code with the CUDA library. The arithmetic lives in ``sense_oracle.c``
 complex128 loops); this module only loads it and marshals numpy arrays.
 
 Functions and the passages they follow:
-  encode       Eq. 4   s = P (S o (m 1^T)), P = e^{o iKR}, S <- S o j (Fig. 2 Alg. 1 step 1)
+  encode       Eq. 4   s = P (S o (m 1^T)), P = e^{o iKR}, S <- S o j (Alg. 1, Fig. 2)
   adjoint      Eq. 5   m = (S* o (P^H Sigma)) 1
-  normal       E^H E m (Fig. 2 Alg. 1 step 8)
-  cg           Fig. 2 Alg. 1 steps 3-18
+  normal       E^H E m (the normal-operator product inside Alg. 1, Fig. 2)
+  cg           the CG loop of Alg. 1 (Fig. 2), then rho <- rho o j
   grad_omega   chain rule of Eq. 4 w.r.t. row 0 of R (the B0 map)
   grad_omega_adjoint  chain rule of Eq. 5 w.r.t. row 0 of R (backward of x = E^H y)
   smooth_map   Eqs. 1 and 3: smoothing and extrapolation of sensitivity / B0 maps as a sparse
                least-squares problem, solved directly
   kspace_mask  the k-space filter: Cartesian points inside the Delaunay triangulation of the
                first-order k-space coordinates (k-space filter section)
-  kspace_filter  rho <- IFFT(FFT(rho) o f), Fig. 2 Alg. 1 step 19, as dense transforms
+  kspace_filter  rho <- IFFT(FFT(rho) o f), the filtering that ends Alg. 1 (Fig. 2),
+                 as dense transforms
   lcurve_corner  maximum-curvature point of the L-curve (log residual norm vs log
                  solution norm over CG iterations), the stopping rule the paper evaluates
 

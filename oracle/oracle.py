@@ -133,7 +133,7 @@ def normal(Kmat, Rmat, S, m, j=None):
 
 def cg(Kmat, Rmat, S, sigma, n_it, j=None, rel_tol=0.0, apply_j=True, history=False,
        iterates=False):
-    """Fig. 2 Alg. 1 steps 3-18. Returns dict(x, iters, history?, iterates?)."""
+    """The CG loop of Alg. 1 (Fig. 2). Returns dict(x, iters, history?, iterates?)."""
     Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
     sigma = _c(sigma, np.complex128).reshape(K, C)
     rho = np.empty(L, np.complex128)
@@ -234,7 +234,7 @@ def kspace_mask(nx, ny, dx, dy, kx, ky):
 
 
 def kspace_filter(image, shape, mask):
-    """rho <- IFFT(FFT(rho) o f) (Fig. 2 Alg. 1 step 19) with the signal model's sign along every
+    """rho <- IFFT(FFT(rho) o f) (the filtering that ends Alg. 1, Fig. 2) with the signal model's sign along every
     axis: F(k_u) = sum_x rho(x) e^{+i 2 pi (u - n/2)(x - n/2) / n}, then
     rho(x) = (1/n) sum_u F(k_u) f(u) e^{-i 2 pi (u - n/2)(x - n/2) / n}, written out as dense
     matrices (shape: (ny, nx) or (nz, ny, nx))."""

@@ -11,11 +11,11 @@
  *
  *   phase      phi(kappa,l) = sum_p K(kappa,p) R(p,l)            Eq. 4, P = e^{o i K R}
  *   encode     s(kappa,lam) = sum_l P(kappa,l) S(l,lam) j(l) m(l) Eq. 4, with S <- S o j
- *                                                                (Fig. 2 Alg. 1 step 1)
+ *                                                                (Alg. 1, Fig. 2)      
  *   adjoint    m(l) = j(l) sum_lam conj(S(l,lam)) sum_kappa conj(P(kappa,l)) s(kappa,lam)
  *                                                                Eq. 5
  *   normal     E^H E m
- *   cg         Fig. 2 Alg. 1 steps 3-18 (CG from rho = 0, N_It iterations)
+ *   cg         the CG loop of Alg. 1, Fig. 2 (from rho = 0, N_It iterations)
  *   grad_omega derivative of a real loss through E w.r.t. row 0 of R (the B0 map),
  *              written as the chain rule of the definition above.
  *
@@ -124,16 +124,16 @@ static cplx dotc(const cplx* a, const cplx* b, int64_t n) { /* a^H b */
 
 static double norm2(const cplx* a, int64_t n) { return sqrt(creal(dotc(a, a, n))); }
 
-/* Fig. 2 Alg. 1 steps 3-18: CG on E^H E rho = E^H sigma from rho = 0.
+/* The CG loop of Alg. 1 (Fig. 2): CG on E^H E rho = E^H sigma from rho = 0.
  *
  *  n_it      N_It, the number of iterations (fixed-count stop, the paper's choice)
  *  rel_tol   extra stop when ||r_n|| <= rel_tol ||r_0|| (0 disables; not in the paper)
- *  rho       output [L]; multiplied by j at the end (step 18) when apply_j != 0
+ *  rho       output [L]; multiplied by j at the end (as Alg. 1 does) when apply_j != 0
  *  hist      optional [(n_it+1)][3]: ||r_n||, ||rho_n||, ||E rho_n - sigma|| for
  *            n = 0..iters (row 0 is the start, rho_0 = 0); unused rows are left as is
- *  iterates  optional [(n_it+1)][L]: rho_n before step 18, n = 0..iters
+ *  iterates  optional [(n_it+1)][L]: rho_n before the final multiplication by j, n = 0..iters
  * Returns the number of iterations run. The update rates are kept complex, as
- * in the listing (alpha = r^H r, beta = p^H q, rho += alpha/beta p ...).      */
+ * Alg. 1 keeps them (alpha = r^H r, beta = p^H q, rho += alpha/beta p ...).      */
 int or_cg(int64_t L, int64_t K, int C, int P1, const double* Km, const double* Rm,
           const cplx* S, const double* j, const cplx* sigma, int n_it, double rel_tol,
           int apply_j, cplx* rho, double* hist, cplx* iterates) {
@@ -143,7 +143,7 @@ int or_cg(int64_t L, int64_t K, int C, int P1, const double* Km, const double* R
   cplx* work = (cplx*)malloc(sizeof(cplx) * (size_t)(K * C));
   cplx* resid = hist ? (cplx*)malloc(sizeof(cplx) * (size_t)(K * C)) : NULL;
 
-  /* step 3: p = E^H sigma ; step 4: r = p ; step 5: rho = 0 */
+  /* start: p = E^H sigma, r = p, rho = 0 */
   or_adjoint(L, K, C, P1, Km, Rm, S, j, sigma, NULL, L, p);
   memcpy(r, p, sizeof(cplx) * (size_t)L);
   for (int64_t l = 0; l < L; ++l) rho[l] = 0.0;
@@ -159,28 +159,28 @@ int or_cg(int64_t L, int64_t K, int C, int P1, const double* Km, const double* R
       hist[3 * n + 2] = norm2(resid, K * C);
     }
     if (iterates) memcpy(iterates + (int64_t)n * L, rho, sizeof(cplx) * (size_t)L);
-    if (n >= n_it) break;                                   /* step 7: n <= N_It */
+    if (n >= n_it) break;                                   /* at most N_It iterations */
     if (rel_tol > 0.0 && norm2(r, L) <= rel_tol * r0) break;
-    /* step 8: q = E^H E p */
+    /* q = E^H E p */
     or_normal(L, K, C, P1, Km, Rm, S, j, p, q, work);
-    /* steps 9-10 */
+    /* alpha = r^H r, beta = p^H q */
     cplx alpha = dotc(r, r, L);
     cplx beta = dotc(p, q, L);
     if (beta == 0.0) break;
-    /* steps 11-12 */
+    /* rho += (alpha / beta) p, r -= (alpha / beta) q */
     const cplx a_over_b = alpha / beta;
     for (int64_t l = 0; l < L; ++l) {
       rho[l] += a_over_b * p[l];
       r[l] -= a_over_b * q[l];
     }
-    /* steps 13-15 */
+    /* new r^H r, ratio to the old one, direction update */
     beta = alpha;
     alpha = dotc(r, r, L);
     const cplx ratio = alpha / beta;
     for (int64_t l = 0; l < L; ++l) p[l] = r[l] + ratio * p[l];
     done = n + 1;
   }
-  /* step 18 */
+  /* rho <- rho o j */
   if (apply_j && j)
     for (int64_t l = 0; l < L; ++l) rho[l] *= j[l];
   free(p);

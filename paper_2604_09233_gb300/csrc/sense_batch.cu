@@ -198,7 +198,7 @@ int batch_normal(sense_batch_s* B, int prec, const std::vector<const float2*>& p
   return SENSE_OK;
 }
 
-// one CG iteration (steps 8-15) of every instance
+// one CG iteration (E^H E p, step length, updates, direction) of every instance
 int batch_cg_iteration(sense_batch_s* B, int prec, cudaStream_t st) {
   std::vector<const float2*> p;
   std::vector<float2*> q;

@@ -75,7 +75,7 @@ __global__ void reduce_xpart_kernel(const float2* __restrict__ Xpart, int nsplit
 }
 
 // ---------------------------------------------------------------------------------------
-// CG kernels (Fig. 2 Alg. 1 steps 3-17)
+// CG kernels (the CG loop of Alg. 1, Fig. 2)
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(VB) data_norm_kernel(const float2* __restrict__ Y, int64_t n,
                                                        double* part, unsigned* counter,
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(VB) data_norm_kernel(const float2* __restrict_
   if (finish_sums<1>(v, part, counter, tot)) scal[SC_SS] = tot[0];
 }
 
-// steps 4-5: r = p = b, rho = 0; rr0 = b^H b; history row 0
+// start: r = p = b, rho = 0; rr0 = b^H b; history row 0
 __global__ void __launch_bounds__(VB) cg_init_kernel(const float2* __restrict__ b, float2* r,
                                                      float2* p, float2* x, int64_t Lp,
                                                      double* part, unsigned* counter,
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(VB) cg_init_kernel(const float2* __restrict__ 
   }
 }
 
-// steps 9-10 and the step length alpha/beta of steps 11-12
+// alpha = r^H r, beta = p^H q and the step length alpha / beta
 __global__ void __launch_bounds__(VB) cg_alpha_kernel(const float2* __restrict__ p,
                                                       const float2* __restrict__ q, int64_t Lp,
                                                       double* part, unsigned* counter,
@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(VB) cg_alpha_kernel(const float2* __restrict__
   }
 }
 
-// steps 11-14 and the history row of the new iterate
+// rho += (alpha/beta) p, r -= (alpha/beta) q, the new r^H r and the history row of the new
+// iterate
 __global__ void __launch_bounds__(VB) cg_update_kernel(float2* x, float2* r,
                                                        const float2* __restrict__ p,
                                                        const float2* __restrict__ q,
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(VB) cg_update_kernel(float2* x, float2* r,
       return;
     }
     scal[SC_RR] = rr;
-    scal[SC_B_RE] = rr / rr_old;   // steps 13-15: alpha_new / beta with beta = alpha_old
+    scal[SC_B_RE] = rr / rr_old;   // alpha_new / beta with beta = alpha_old
     scal[SC_B_IM] = 0.0;
     if (scal[SC_TOL2] > 0.0 && rr <= scal[SC_TOL2]) scal[SC_STOP] = 1.0;
   }
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(VB) cg_replace_kernel(const float2* __restrict
   }
 }
 
-// step 15
+// direction update p = r + (alpha_new / alpha_old) p
 __global__ void cg_p_kernel(float2* p, const float2* __restrict__ r, int64_t Lp,
                             const double* scal) {
   if (stopped(scal)) return;
@@ -333,7 +334,7 @@ int adjoint_internal(sense_plan_s* P, int prec, const float2* Y, float2* q, cons
   return reduce_xpart(P, q, stop, st);
 }
 
-// one launch each of steps 9-12, 11-14 and 15 on the plan's CG vectors
+// one launch each of the step-length, update and direction kernels on the plan's CG vectors
 int cg_step_alpha(sense_plan_s* P, cudaStream_t st) {
   cg_alpha_kernel<<<grid_for(P, P->Lp), VB, 0, st>>>(P->vp, P->vq, P->Lp, P->red, P->counter,
                                                      P->scal);
@@ -501,7 +502,7 @@ int cg_begin(sense_plan_s* P, const float2* s, const sense_cg_opts* opts, double
   data_norm_kernel<<<yb, VB, 0, st>>>(P->Ydata, P->Kp * P->Cp, P->red, P->counter, P->scal);
   SENSE_CUDA_TRY(cudaGetLastError());
   count_launch(P);
-  // step 3: b = E^H sigma (FP32 operator, or the split tensor-core operator when the
+  // b = E^H sigma (FP32 operator, or the split tensor-core operator when the
   // iterations use it; FP32 whenever the residual is refined: b enters every replaced
   // residual)
   const int prec_b = (opts->prec == SENSE_PREC_TC_SPLIT && opts->refine_every == 0)
@@ -555,7 +556,7 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
   if (iterates) SENSE_CUDA_TRY(cudaMemsetAsync(iterates, 0, (size_t)P->L * 8, st));
   for (int n = 0; n < N; ++n) {
     if (ckpt_every > 0 && n % ckpt_every == 0) TRY(ckpt_save(P, ckpt, n / ckpt_every, st));
-    // step 8
+    // q = E^H E p
     TRY(apply_normal_internal(P, opts->prec, P->vp, P->vq, stop, st));
     TRY(cg_step_alpha(P, st));
     TRY(cg_step_update(P, P->hist, st));
@@ -574,7 +575,7 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
       TRY(scatter_image(P, P->vx, iterates + (size_t)(n + 1) * P->L, opts->apply_j != 0, st));
   }
   if (ckpt_every > 0) TRY(ckpt_final(P, ckpt, st));
-  // step 18
+  // rho <- rho o j
   TRY(scatter_image(P, P->vx, (float2*)out.dev, opts->apply_j != 0, st));
   if (history || info) {
     int iters = 0;

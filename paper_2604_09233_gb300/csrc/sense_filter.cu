@@ -1,4 +1,4 @@
-// k-space filter: rho <- IFFT(FFT(rho) o f) (Fig. 2, Alg. 1 step 19).
+// k-space filter: rho <- IFFT(FFT(rho) o f) (the filtering that ends Alg. 1, Fig. 2).
 //
 // The filter keeps the Cartesian k-space points that lie inside the convex hull of the
 // first-order field coefficients (the k-space coordinates of the samples): components far from

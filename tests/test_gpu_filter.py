@@ -1,4 +1,4 @@
-"""The k-space filter (Fig. 2 Alg. 1 step 19) through the C ABI against the oracle's dense
+"""The k-space filter that ends Alg. 1 (Fig. 2) through the C ABI against the oracle's dense
 transforms."""
 import numpy as np
 import pytest

@@ -141,7 +141,7 @@ def test_cg_converges_to_dense_normal_solution(tiny):
     x_star = np.linalg.solve(A, b)
     out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 4 * wl.L, j=wl.j, apply_j=False)
     assert _rel(out["x"], x_star) < 1e-9
-    # step 18: the output is multiplied by j
+    # Alg. 1 ends by multiplying the output by j
     out_j = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 4 * wl.L, j=wl.j, apply_j=True)
     assert _rel(out_j["x"], x_star * wl.j) < 1e-9
 
