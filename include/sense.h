@@ -251,14 +251,20 @@ int sense_kspace_filter(int32_t nx, int32_t ny, int32_t nz, const float* mask, f
  * next voxel exists; a row is weighted by wd at its voxel; axes of length 1 have none.
  * w0, wd [n] float, xhat, x [n] complex64 (real maps: zero imaginary parts), DEVICE memory;
  * x may equal xhat. Voxels that no equation constrains (w0 = 0 and no weighted derivative row
- * touches them) keep xhat. info (nullable): iterations run and the final relative residual of the
- * normal equations. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+ * touches them) keep xhat. precond selects plain CG or CG preconditioned by one symmetric
+ * multigrid V-cycle (Galerkin coarse operators of linear interpolation, Chebyshev smoothing on
+ * the diagonal; built on the device at every call; the paper's incomplete-Cholesky choice is
+ * sequential and is not offered). info (nullable): iterations run and the final relative
+ * residual of the normal equations. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+#define SENSE_SMOOTH_PLAIN 0
+#define SENSE_SMOOTH_MULTIGRID 1
 typedef struct {
   int32_t nx, ny, nz;
   int32_t order;      /* 1 or 2                                                         */
   double alpha;       /* smoothness weight (alpha_B or alpha_S)                         */
   int32_t max_iter;
   double rel_tol;     /* stop when ||r|| <= rel_tol ||diag(w0^2) xhat||                 */
+  int32_t precond;    /* SENSE_SMOOTH_PLAIN or SENSE_SMOOTH_MULTIGRID                   */
 } sense_smooth_opts;
 
 typedef struct {

@@ -30,12 +30,16 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* sh /* [N][VB/3
     }
 }
 
-// Writes this block's sums; returns true (in thread 0 only) if this block finished last,
-// in which case tot[] holds the totals over all blocks in block order.
+// Writes this block's sums; returns true (in thread 0 only) if this block finished last, in
+// which case tot[] holds the totals over all blocks. The last block adds the partials with all
+// its threads (thread t takes partials t, t + VB, ... in order, then the fixed tree of
+// block_sum), so the totals depend only on the grid size and are the same on every run.
+// Every thread of the block must call it (it synchronises the block).
 template <int N>
 __device__ __forceinline__ bool finish_sums(double (&v)[N], double* part, unsigned* counter,
                                             double (&tot)[N]) {
   __shared__ bool last;
+  __shared__ double sh[N * (VB / 32)];
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < N; ++j) part[blockIdx.x * N + j] = v[j];
@@ -44,13 +48,18 @@ __device__ __forceinline__ bool finish_sums(double (&v)[N], double* part, unsign
     last = (done == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return false;
+  if (!last) return false;
   __threadfence();
+  double a[N];
 #pragma unroll
-  for (int j = 0; j < N; ++j) tot[j] = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b)
+  for (int j = 0; j < N; ++j) a[j] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
-    for (int j = 0; j < N; ++j) tot[j] += ((volatile double*)part)[b * N + j];
+    for (int j = 0; j < N; ++j) a[j] += ((volatile double*)part)[b * N + j];
+  block_sum<N>(a, sh);
+  if (threadIdx.x != 0) return false;
+#pragma unroll
+  for (int j = 0; j < N; ++j) tot[j] = a[j];
   *counter = 0u;
   return true;
 }

@@ -73,7 +73,8 @@ class CGOpts(ctypes.Structure):
 class SmoothOpts(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("alpha", ctypes.c_double),
-                ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double)]
+                ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
+                ("precond", ctypes.c_int32)]
 
 
 class SmoothInfo(ctypes.Structure):
@@ -275,13 +276,18 @@ def sense_plan_store_p(plan, enable=True, stream=None):
     _check(_lib.sense_plan_store_p(plan, 1 if enable else 0, stream), "sense_plan_store_p")
 
 
+SMOOTH_PRECOND = {"none": 0, "multigrid": 1}
+
+
 def sense_smooth_map(shape, order, alpha, w0, wd, xhat, x, max_iter=2000, rel_tol=1e-7,
-                     stream=None):
+                     precond="multigrid", stream=None):
     """Eq. 1 (order 2) / Eq. 3 (order 1) smoothing on a grid of `shape` ((ny, nx) or
-    (nz, ny, nx)); w0, wd float32 and xhat, x complex64 CUDA tensors. Returns the info dict."""
+    (nz, ny, nx)); w0, wd float32 and xhat, x complex64 CUDA tensors; precond "multigrid"
+    (V-cycle preconditioned CG) or "none" (plain CG). Returns the info dict."""
     nz, ny, nx = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
+    pc = SMOOTH_PRECOND[precond] if isinstance(precond, str) else int(precond)
     o = SmoothOpts(int(nx), int(ny), int(nz), int(order), float(alpha), int(max_iter),
-                   float(rel_tol))
+                   float(rel_tol), pc)
     info = SmoothInfo()
     p0, _, s0 = _ptr(w0, np.float32)
     p1, _, _ = _ptr(wd, np.float32)
