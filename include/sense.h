@@ -249,13 +249,15 @@ int sense_kspace_filter(int32_t nx, int32_t ny, int32_t nz, const float* mask, f
  * w0 = 1, wd = the standard error of the phase fit), through its normal equations by CG from
  * x = xhat. Second-difference rows exist at interior voxels, first-difference rows where the
  * next voxel exists; a row is weighted by wd at its voxel; axes of length 1 have none.
- * w0, wd [n] float, xhat, x [n] complex64 (real maps: zero imaginary parts), DEVICE memory;
- * x may equal xhat. Voxels that no equation constrains (w0 = 0 and no weighted derivative row
- * touches them) keep xhat. precond selects plain CG or CG preconditioned by one symmetric
- * multigrid V-cycle (Galerkin coarse operators of linear interpolation, Chebyshev smoothing on
- * the diagonal; built on the device at every call; the paper's incomplete-Cholesky choice is
- * sequential and is not offered). info (nullable): iterations run and the final relative
- * residual of the normal equations. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+ * n_fields right-hand sides share w0 and wd and are solved together, each with its own CG
+ * scalars and stop test: xhat, x are [n_fields][n] complex64 (real maps: zero imaginary parts),
+ * w0, wd [n] float, all DEVICE memory; x may equal xhat. Voxels that no equation constrains
+ * (w0 = 0 and no weighted derivative row touches them) keep xhat. precond selects plain CG or CG
+ * preconditioned by one symmetric multigrid V-cycle (Galerkin coarse operators of linear
+ * interpolation, Chebyshev smoothing on the diagonal; built on the device at every call; the
+ * paper's incomplete-Cholesky choice is sequential and is not offered). info (nullable):
+ * [n_fields] host entries, iterations run and the final relative residual of the normal
+ * equations per field. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
 #define SENSE_SMOOTH_PLAIN 0
 #define SENSE_SMOOTH_MULTIGRID 1
 typedef struct {
@@ -265,6 +267,7 @@ typedef struct {
   int32_t max_iter;
   double rel_tol;     /* stop when ||r|| <= rel_tol ||diag(w0^2) xhat||                 */
   int32_t precond;    /* SENSE_SMOOTH_PLAIN or SENSE_SMOOTH_MULTIGRID                   */
+  int32_t n_fields;   /* right-hand sides, 1..65535                                     */
 } sense_smooth_opts;
 
 typedef struct {
@@ -274,6 +277,17 @@ typedef struct {
 
 int sense_smooth_map(const sense_smooth_opts* opts, const float* w0, const float* wd,
                      const float* xhat, float* x, sense_smooth_info* info, void* stream);
+
+/* Sensitivity maps as the paper processes them with Eq. 1 (section on sensitivity maps): for
+ * every coil the magnitude |S_hat| and the magnitude-normalised map S_hat / |S_hat| (0 where
+ * S_hat = 0) are smoothed separately, then recombined as S = m u / |u| (m the smoothed
+ * magnitude, u the smoothed normalised map; 0 where u = 0). All 2 C fields are solved in one
+ * call of the solver above (opts->n_fields is ignored). S_hat, S: [L][C] complex64 (coil
+ * fastest, L = nx ny nz raster order), DEVICE memory, may alias. info (nullable): [2 C] host
+ * entries, magnitudes first. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+int sense_smooth_sensitivities(const sense_smooth_opts* opts, int32_t C, const float* w0,
+                               const float* wd, const float* S_hat, float* S,
+                               sense_smooth_info* info, void* stream);
 
 /* Batched reconstruction -----------------------------------------------------------------
  * (no counterpart in the paper, which reconstructs one slice or volume at a time)

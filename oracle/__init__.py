@@ -14,6 +14,8 @@ Functions and the passages they follow:
   grad_omega_adjoint  chain rule of Eq. 5 w.r.t. row 0 of R (backward of x = E^H y)
   smooth_map   Eqs. 1 and 3: smoothing and extrapolation of sensitivity / B0 maps as a sparse
                least-squares problem, solved directly
+  smooth_sensitivities  Eq. 1 per coil on the magnitude and the magnitude-normalised map,
+               recombined (sensitivity-map section)
   kspace_mask  the k-space filter: Cartesian points inside the Delaunay triangulation of the
                first-order k-space coordinates (k-space filter section)
   kspace_filter  rho <- IFFT(FFT(rho) o f), the filtering that ends Alg. 1 (Fig. 2),
@@ -37,6 +39,7 @@ from .oracle import (  # noqa: F401
     kspace_mask,
     kspace_filter,
     smooth_map,
+    smooth_sensitivities,
     lcurve_corner,
     num_threads,
     set_num_threads,

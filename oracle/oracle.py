@@ -220,6 +220,24 @@ def smooth_map(shape, order, alpha, w0, wd, xhat):
     return x
 
 
+def smooth_sensitivities(shape, alpha, m_t, m_r, S_hat):
+    """Sensitivity maps by Eq. 1 as the paper applies it: for every coil the magnitude of
+    S_hat and the magnitude-normalised S_hat (0 where S_hat = 0) are smoothed separately (w0 =
+    M_T, wd = M_R, second differences) and recombined as S = m u / |u| (0 where u = 0).
+    S_hat: [n][C] complex; returns [n][C]."""
+    S_hat = np.asarray(S_hat, complex)
+    n, C = S_hat.shape
+    out = np.zeros((n, C), complex)
+    for c in range(C):
+        mag = np.abs(S_hat[:, c])
+        unit = np.where(mag > 0, S_hat[:, c] / np.where(mag > 0, mag, 1.0), 0.0)
+        m = smooth_map(shape, 2, alpha, m_t, m_r, mag.astype(complex)).real
+        u = smooth_map(shape, 2, alpha, m_t, m_r, unit)
+        a = np.abs(u)
+        out[:, c] = np.where(a > 0, m * u / np.where(a > 0, a, 1.0), 0.0)
+    return out
+
+
 def kspace_mask(nx, ny, dx, dy, kx, ky):
     """k-space filter of the paper's k-space filter section: 1 for the Cartesian k-space
     points 2 pi (u - n/2) / (n d) that lie in a triangle of the Delaunay triangulation of the

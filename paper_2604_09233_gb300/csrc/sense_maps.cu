@@ -28,9 +28,15 @@
 //    thread block.
 // The cycle's output is zeroed at unconstrained voxels, so those keep xhat as in plain CG.
 //
-// Each CG iteration is captured once in a CUDA graph and replayed; the host reads the device's
-// stop flag (tolerance reached or breakdown) one batch of replays behind, and every kernel
-// returns at once after the flag is set.
+// Several fields (right-hand sides) are solved together: the matrix depends only on w0, wd and
+// alpha, so one hierarchy serves them all, and every kernel runs over all fields at once (the
+// second grid dimension), each field with its own CG scalars and stop flag. The paper smooths the
+// magnitude and the magnitude-normalised map of every coil; sense_smooth_sensitivities makes
+// those 2 C fields, solves them in one call and recombines them.
+//
+// Each CG iteration is captured once in a CUDA graph and replayed; the host reads the count of
+// stopped fields (tolerance reached or breakdown) one batch of replays behind, and every kernel
+// returns at once for a field that has stopped.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -132,191 +138,172 @@ __device__ __forceinline__ float2 drow(const Grid& g, const float2* x, long long
 }
 
 // ---------------------------------------------------------------------------------------
-// CG on the normal equations
+// CG on the normal equations, for F fields at once (blockIdx.y = field; field f's vectors
+// start at f * n, its scalars at sc + 8 f, its reduction partials at part + f * pstride and
+// its completion counter at counter[f]). Every kernel skips the fields that have stopped.
 // ---------------------------------------------------------------------------------------
 
-// y = w0^2 x + alpha sum_d D_d^T diag(wd^2) D_d x (matrix-free)
-__global__ void smooth_apply_kernel(Grid g, int order, float alpha, const float* __restrict__ w0,
-                                    const float* __restrict__ wd, const float2* __restrict__ x,
-                                    float2* __restrict__ y, const double* sc) {
-  if (sc[2] != 0.0) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.total;
-       i += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    coords(g, i, c);
-    const float a0 = w0[i] * w0[i];
-    float2 acc = make_float2(a0 * x[i].x, a0 * x[i].y);
-    for (int d = 0; d < 3; ++d) {
-      const int n = g.n[d];
-      if (n < 2) continue;
-      const long long s = g.stride[d];
-      float2 t = make_float2(0.f, 0.f);
-      if (order == 1) {
-        // rows r = i - 1 (coefficient +1 on x[i]) and r = i (coefficient -1)
-        if (c[d] >= 1) {
-          const float w = wd[i - s] * wd[i - s];
-          const float2 v = drow(g, x, i - s, d, 1);
-          t.x += w * v.x;
-          t.y += w * v.y;
-        }
-        if (c[d] + 1 < n) {
-          const float w = wd[i] * wd[i];
-          const float2 v = drow(g, x, i, d, 1);
-          t.x -= w * v.x;
-          t.y -= w * v.y;
-        }
-      } else {
-        // rows r = i - 1 and i + 1 (coefficient +1 on x[i]) and r = i (coefficient -2)
-        if (c[d] >= 2) {
-          const float w = wd[i - s] * wd[i - s];
-          const float2 v = drow(g, x, i - s, d, 2);
-          t.x += w * v.x;
-          t.y += w * v.y;
-        }
-        if (c[d] >= 1 && c[d] + 1 < n) {
-          const float w = wd[i] * wd[i];
-          const float2 v = drow(g, x, i, d, 2);
-          t.x -= 2.f * w * v.x;
-          t.y -= 2.f * w * v.y;
-        }
-        if (c[d] + 2 < n) {
-          const float w = wd[i + s] * wd[i + s];
-          const float2 v = drow(g, x, i + s, d, 2);
-          t.x += w * v.x;
-          t.y += w * v.y;
-        }
-      }
-      acc.x += alpha * t.x;
-      acc.y += alpha * t.y;
-    }
-    y[i] = acc;
+// Scalars of a field: 0 r^H r, 1 ||b||^2, 2 stop flag, 3 step length, 4 beta, 5 iterations,
+// 6 r^H z (preconditioned). nstop counts the fields that have stopped.
+constexpr int NSC = 8;
+
+__device__ __forceinline__ void set_stop(double* s, unsigned* nstop) {
+  if (s[2] == 0.0) {
+    s[2] = 1.0;
+    atomicAdd(nstop, 1u);
   }
 }
 
-// Scalars sc[]: 0 r^H r, 1 ||b||^2, 2 stop flag, 3 step length, 4 beta, 5 iterations,
-// 6 r^H z (preconditioned).
-
-// r = w0^2 xhat - y (y = N x_0), p = r; sums ||r||^2 and ||w0^2 xhat||^2
+// r = w0^2 xhat - y (y = N x_0), p = r; sums ||r||^2 and ||w0^2 xhat||^2 and the stop test
 __global__ void __launch_bounds__(VB) smooth_init_kernel(const float* __restrict__ w0,
-                                                         const float2* __restrict__ xhat,
-                                                         const float2* __restrict__ y,
-                                                         long long n, float2* r, float2* p,
-                                                         double* part, unsigned* counter,
-                                                         double* sc, double tol2) {
+                                                         const float2* __restrict__ xhatb,
+                                                         const float2* __restrict__ yb,
+                                                         long long n, float2* rb, float2* pb,
+                                                         double* part, long long pstride,
+                                                         unsigned* counter, double* sc,
+                                                         unsigned* nstop, double tol2) {
   __shared__ double sh[2 * VB / 32];
-  double v[2] = {0.0, 0.0};
+  const int f = blockIdx.y;
+  const long long o = (long long)f * n;
+  // per-thread partials in FP32 (a few elements each), block and grid sums in FP64
+  float a[2] = {0.f, 0.f};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const float a0 = w0[i] * w0[i];
-    const float2 b = make_float2(a0 * xhat[i].x, a0 * xhat[i].y);
-    const float2 ri = make_float2(b.x - y[i].x, b.y - y[i].y);
-    r[i] = ri;
-    p[i] = ri;
-    v[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
-    v[1] += (double)b.x * b.x + (double)b.y * b.y;
+    const float2 xh = xhatb[o + i], y = yb[o + i];
+    const float2 b = make_float2(a0 * xh.x, a0 * xh.y);
+    const float2 ri = make_float2(b.x - y.x, b.y - y.y);
+    rb[o + i] = ri;
+    pb[o + i] = ri;
+    a[0] = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, a[0]));
+    a[1] = fmaf(b.x, b.x, fmaf(b.y, b.y, a[1]));
   }
+  double v[2] = {(double)a[0], (double)a[1]};
   block_sum<2>(v, sh);
   double tot[2];
-  if (finish_sums<2>(v, part, counter, tot)) {
-    sc[0] = tot[0];   // r^H r
-    sc[1] = tot[1];   // ||b||^2
-    sc[2] = tot[0] <= tol2 * tot[1] ? 1.0 : 0.0;   // stop flag
+  if (finish_sums<2>(v, part + f * pstride, counter + f, tot)) {
+    double* s = sc + f * NSC;
+    s[0] = tot[0];   // r^H r
+    s[1] = tot[1];   // ||b||^2
+    if (tot[0] <= tol2 * tot[1]) set_stop(s, nstop);
   }
 }
 
 // step length = (r^H z or r^H r) / p^H N p (N real symmetric: p^H N p real)
-__global__ void __launch_bounds__(VB) smooth_pap_kernel(const float2* __restrict__ p,
-                                                        const float2* __restrict__ q, long long n,
-                                                        double* part, unsigned* counter,
-                                                        double* sc, int num) {
-  if (sc[2] != 0.0) return;
+__global__ void __launch_bounds__(VB) smooth_pap_kernel(const float2* __restrict__ pb,
+                                                        const float2* __restrict__ qb, long long n,
+                                                        double* part, long long pstride,
+                                                        unsigned* counter, double* sc,
+                                                        unsigned* nstop, int num) {
+  const int f = blockIdx.y;
+  double* s = sc + f * NSC;
+  if (s[2] != 0.0) return;
   __shared__ double sh[VB / 32];
-  double v[1] = {0.0};
+  const float2* p = pb + (long long)f * n;
+  const float2* q = qb + (long long)f * n;
+  float a = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    v[0] += (double)p[i].x * q[i].x + (double)p[i].y * q[i].y;
+    a = fmaf(p[i].x, q[i].x, fmaf(p[i].y, q[i].y, a));
+  double v[1] = {(double)a};
   block_sum<1>(v, sh);
   double tot[1];
-  if (finish_sums<1>(v, part, counter, tot)) {
+  if (finish_sums<1>(v, part + f * pstride, counter + f, tot)) {
     if (!(tot[0] > 0.0)) {
-      sc[2] = 1.0;
+      set_stop(s, nstop);
       return;
     }
-    sc[3] = sc[num] / tot[0];
+    s[3] = s[num] / tot[0];
   }
 }
 
 // x += a p; r -= a q; the new r^H r, beta for plain CG, the iteration count and the stop test
-__global__ void __launch_bounds__(VB) smooth_update_kernel(float2* x, float2* r,
-                                                           const float2* __restrict__ p,
-                                                           const float2* __restrict__ q,
+__global__ void __launch_bounds__(VB) smooth_update_kernel(float2* xb, float2* rb,
+                                                           const float2* __restrict__ pb,
+                                                           const float2* __restrict__ qb,
                                                            long long n, double* part,
-                                                           unsigned* counter, double* sc,
+                                                           long long pstride, unsigned* counter,
+                                                           double* sc, unsigned* nstop,
                                                            double tol2) {
-  if (sc[2] != 0.0) return;
+  const int f = blockIdx.y;
+  double* s = sc + f * NSC;
+  if (s[2] != 0.0) return;
   __shared__ double sh[VB / 32];
-  const float a = (float)sc[3];
-  double v[1] = {0.0};
+  const long long o = (long long)f * n;
+  const float a = (float)s[3];
+  float acc = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    x[i].x += a * p[i].x;
-    x[i].y += a * p[i].y;
-    const float2 ri = make_float2(r[i].x - a * q[i].x, r[i].y - a * q[i].y);
-    r[i] = ri;
-    v[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    const float2 pi = pb[o + i], qi = qb[o + i];
+    float2 xi = xb[o + i];
+    xi.x += a * pi.x;
+    xi.y += a * pi.y;
+    xb[o + i] = xi;
+    const float2 ri = make_float2(rb[o + i].x - a * qi.x, rb[o + i].y - a * qi.y);
+    rb[o + i] = ri;
+    acc = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, acc));
   }
+  double v[1] = {(double)acc};
   block_sum<1>(v, sh);
   double tot[1];
-  if (finish_sums<1>(v, part, counter, tot)) {
-    sc[4] = tot[0] / sc[0];   // beta (plain CG)
-    sc[0] = tot[0];
-    sc[5] += 1.0;             // iterations
-    if (tot[0] <= tol2 * sc[1]) sc[2] = 1.0;
+  if (finish_sums<1>(v, part + f * pstride, counter + f, tot)) {
+    s[4] = tot[0] / s[0];   // beta (plain CG)
+    s[0] = tot[0];
+    s[5] += 1.0;            // iterations
+    if (tot[0] <= tol2 * s[1]) set_stop(s, nstop);
   }
 }
 
 // Preconditioned CG: z <- 0 at unconstrained voxels, r^H z, beta = r^H z / (previous r^H z)
 // (first = 1: beta = 0, so that the next direction is z itself)
-__global__ void __launch_bounds__(VB) smooth_rz_kernel(float2* z, const float2* __restrict__ r,
+__global__ void __launch_bounds__(VB) smooth_rz_kernel(float2* zb, const float2* __restrict__ rb,
                                                        const unsigned char* __restrict__ keep,
                                                        long long n, double* part,
-                                                       unsigned* counter, double* sc, int first) {
-  if (sc[2] != 0.0) return;
+                                                       long long pstride, unsigned* counter,
+                                                       double* sc, unsigned* nstop, int first) {
+  const int f = blockIdx.y;
+  double* s = sc + f * NSC;
+  if (s[2] != 0.0) return;
   __shared__ double sh[VB / 32];
-  double v[1] = {0.0};
+  const long long o = (long long)f * n;
+  float a = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    float2 zi = z[i];
+    float2 zi = zb[o + i];
     if (!keep[i]) {
       zi = make_float2(0.f, 0.f);
-      z[i] = zi;
+      zb[o + i] = zi;
     }
-    v[0] += (double)r[i].x * zi.x + (double)r[i].y * zi.y;
+    a = fmaf(rb[o + i].x, zi.x, fmaf(rb[o + i].y, zi.y, a));
   }
+  double v[1] = {(double)a};
   block_sum<1>(v, sh);
   double tot[1];
-  if (finish_sums<1>(v, part, counter, tot)) {
+  if (finish_sums<1>(v, part + f * pstride, counter + f, tot)) {
     if (!(tot[0] > 0.0)) {
-      sc[2] = 1.0;   // breakdown (or r = 0)
+      set_stop(s, nstop);   // breakdown (or r = 0)
       return;
     }
-    sc[4] = first ? 0.0 : tot[0] / sc[6];
-    sc[6] = tot[0];
+    s[4] = first ? 0.0 : tot[0] / s[6];
+    s[6] = tot[0];
   }
 }
 
 // p = z + beta p (z = r for plain CG)
-__global__ void smooth_p_kernel(float2* p, const float2* __restrict__ z, long long n,
+__global__ void smooth_p_kernel(float2* pb, const float2* __restrict__ zb, long long n,
                                 const double* sc) {
-  if (sc[2] != 0.0) return;
-  const float b = (float)sc[4];
+  const int f = blockIdx.y;
+  const double* s = sc + f * NSC;
+  if (s[2] != 0.0) return;
+  const long long o = (long long)f * n;
+  const float b = (float)s[4];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    p[i] = make_float2(z[i].x + b * p[i].x, z[i].y + b * p[i].y);
+    pb[o + i] = make_float2(zb[o + i].x + b * pb[o + i].x, zb[o + i].y + b * pb[o + i].y);
 }
 
 // ---------------------------------------------------------------------------------------
-// Multigrid hierarchy
+// Multigrid hierarchy (shared by all fields)
 // ---------------------------------------------------------------------------------------
 
 // Level 0: N as a cross stencil of half-width `order` along every axis longer than 1.
@@ -517,83 +504,238 @@ __global__ void mg_normalize_kernel(const float2* __restrict__ w, float2* v, lon
 }
 
 // ---------------------------------------------------------------------------------------
-// V-cycle kernels (all return at once after the CG stop flag is set)
+// V-cycle kernels: blockIdx.y = field, vectors of level size n at f * n (the coarsest-grid
+// kernel: one block per field); each returns at once for a field whose CG has stopped
 // ---------------------------------------------------------------------------------------
 
 // Chebyshev start from x = 0: r = b, d = D^-1 b / theta, x = d
 __global__ void cheb_first0_kernel(long long n, const float* __restrict__ dinv,
-                                   const float2* __restrict__ b, float2* x, float2* r, float2* d,
-                                   float inv_theta, const double* sc) {
-  if (sc[2] != 0.0) return;
+                                   const float2* __restrict__ bb, float2* xb, float2* rb,
+                                   float2* db, float inv_theta, const double* sc) {
+  const int f = blockIdx.y;
+  if (sc[f * NSC + 2] != 0.0) return;
+  const long long o = (long long)f * n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float2 bi = b[i];
+    const float2 bi = bb[o + i];
     const float s = dinv[i] * inv_theta;
     const float2 di = make_float2(s * bi.x, s * bi.y);
-    r[i] = bi;
-    d[i] = di;
-    x[i] = di;
+    rb[o + i] = bi;
+    db[o + i] = di;
+    xb[o + i] = di;
+  }
+}
+
+// Stencil kernels take the fields in chunks of FC (blockIdx.y = chunk), so that every
+// coefficient is loaded once per voxel and applied to FC fields.
+constexpr int FC = 8;
+
+// bit k set: field f0 + k exists and has not stopped (f0 = first field of this block's chunk)
+__device__ __forceinline__ unsigned chunk_active(int F, const double* sc, int& f0) {
+  f0 = blockIdx.y * FC;
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < FC; ++k)
+    if (f0 + k < F && sc[(f0 + k) * NSC + 2] == 0.0) m |= 1u << k;
+  return m;
+}
+
+// acc[k] = (A v_{f0 + k})_i for the active fields of the chunk
+__device__ __forceinline__ void sten_apply_chunk(const Grid& g, const Sten& s, const float* c,
+                                                 const float2* vb, long long i,
+                                                 const int (&ci)[3], int f0, unsigned act,
+                                                 float2 (&acc)[FC]) {
+#pragma unroll
+  for (int k = 0; k < FC; ++k) acc[k] = make_float2(0.f, 0.f);
+  for_offsets(s, [&](int o, int dx, int dy, int dz) {
+    const int x = ci[0] + dx, y = ci[1] + dy, z = ci[2] + dz;
+    if (x < 0 || x >= g.n[0] || y < 0 || y >= g.n[1] || z < 0 || z >= g.n[2]) return;
+    const float a = c[(long long)o * g.total + i];
+    if (a == 0.f) return;
+    const long long j = i + dx * g.stride[0] + dy * g.stride[1] + dz * g.stride[2];
+#pragma unroll
+    for (int k = 0; k < FC; ++k)
+      if ((act >> k) & 1u) {
+        const float2 w = vb[(long long)(f0 + k) * g.total + j];
+        acc[k].x = fmaf(a, w.x, acc[k].x);
+        acc[k].y = fmaf(a, w.y, acc[k].y);
+      }
+  });
+}
+
+// y = w0^2 x + alpha sum_d D_d^T diag(wd^2) D_d x, matrix-free (the differences are taken of x
+// itself, so fields in the null space of D stay there exactly), FC fields per block
+__global__ void smooth_apply_kernel(Grid g, int order, float alpha, const float* __restrict__ w0,
+                                    const float* __restrict__ wd, const float2* __restrict__ xb,
+                                    float2* __restrict__ yb, int F, const double* sc) {
+  int f0;
+  const unsigned act = chunk_active(F, sc, f0);
+  if (!act) return;
+  const long long n = g.total;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords(g, i, c);
+    const float a0 = w0[i] * w0[i];
+    float2 acc[FC];
+#pragma unroll
+    for (int k = 0; k < FC; ++k) {
+      acc[k] = make_float2(0.f, 0.f);
+      if ((act >> k) & 1u) {
+        const float2 xi = xb[(long long)(f0 + k) * n + i];
+        acc[k] = make_float2(a0 * xi.x, a0 * xi.y);
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      const int nd = g.n[d];
+      if (nd < 2) continue;
+      const long long s = g.stride[d];
+      if (order == 1) {
+        // rows r = i - 1 (coefficient +1 on x[i]) and r = i (coefficient -1)
+        const bool lo = c[d] >= 1, hi = c[d] + 1 < nd;
+        const float wl = lo ? wd[i - s] * wd[i - s] : 0.f;
+        const float wh = hi ? wd[i] * wd[i] : 0.f;
+#pragma unroll
+        for (int k = 0; k < FC; ++k) {
+          if (!((act >> k) & 1u)) continue;
+          const float2* x = xb + (long long)(f0 + k) * n;
+          float2 t = make_float2(0.f, 0.f);
+          if (lo) {
+            const float2 v = drow(g, x, i - s, d, 1);
+            t.x += wl * v.x;
+            t.y += wl * v.y;
+          }
+          if (hi) {
+            const float2 v = drow(g, x, i, d, 1);
+            t.x -= wh * v.x;
+            t.y -= wh * v.y;
+          }
+          acc[k].x += alpha * t.x;
+          acc[k].y += alpha * t.y;
+        }
+      } else {
+        // rows r = i - 1 and i + 1 (coefficient +1 on x[i]) and r = i (coefficient -2)
+        const bool ra = c[d] >= 2, rb = c[d] >= 1 && c[d] + 1 < nd, rc = c[d] + 2 < nd;
+        const float wa = ra ? wd[i - s] * wd[i - s] : 0.f;
+        const float wb = rb ? wd[i] * wd[i] : 0.f;
+        const float wc = rc ? wd[i + s] * wd[i + s] : 0.f;
+#pragma unroll
+        for (int k = 0; k < FC; ++k) {
+          if (!((act >> k) & 1u)) continue;
+          const float2* x = xb + (long long)(f0 + k) * n;
+          float2 t = make_float2(0.f, 0.f);
+          if (ra) {
+            const float2 v = drow(g, x, i - s, d, 2);
+            t.x += wa * v.x;
+            t.y += wa * v.y;
+          }
+          if (rb) {
+            const float2 v = drow(g, x, i, d, 2);
+            t.x -= 2.f * wb * v.x;
+            t.y -= 2.f * wb * v.y;
+          }
+          if (rc) {
+            const float2 v = drow(g, x, i + s, d, 2);
+            t.x += wc * v.x;
+            t.y += wc * v.y;
+          }
+          acc[k].x += alpha * t.x;
+          acc[k].y += alpha * t.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < FC; ++k)
+      if ((act >> k) & 1u) yb[(long long)(f0 + k) * n + i] = acc[k];
   }
 }
 
 // Chebyshev start from x: r = b - A x, d = D^-1 r / theta, xo = x + d
 __global__ void cheb_first_kernel(Grid g, Sten s, const float* __restrict__ c,
-                                  const float* __restrict__ dinv, const float2* __restrict__ b,
-                                  const float2* __restrict__ x, float2* xo, float2* r, float2* d,
-                                  float inv_theta, const double* sc) {
-  if (sc[2] != 0.0) return;
+                                  const float* __restrict__ dinv, const float2* __restrict__ bb,
+                                  const float2* __restrict__ xb, float2* xob, float2* rb,
+                                  float2* db, float inv_theta, int F, const double* sc) {
+  int f0;
+  const unsigned act = chunk_active(F, sc, f0);
+  if (!act) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.total;
        i += (long long)gridDim.x * blockDim.x) {
     int ci[3];
     coords(g, i, ci);
-    const float2 a = sten_apply(g, s, c, x, i, ci);
-    const float2 ri = make_float2(b[i].x - a.x, b[i].y - a.y);
+    float2 a[FC];
+    sten_apply_chunk(g, s, c, xb, i, ci, f0, act, a);
     const float t = dinv[i] * inv_theta;
-    const float2 di = make_float2(t * ri.x, t * ri.y);
-    r[i] = ri;
-    d[i] = di;
-    xo[i] = make_float2(x[i].x + di.x, x[i].y + di.y);
+#pragma unroll
+    for (int k = 0; k < FC; ++k)
+      if ((act >> k) & 1u) {
+        const long long o = (long long)(f0 + k) * g.total + i;
+        const float2 ri = make_float2(bb[o].x - a[k].x, bb[o].y - a[k].y);
+        const float2 di = make_float2(t * ri.x, t * ri.y);
+        rb[o] = ri;
+        db[o] = di;
+        xob[o] = make_float2(xb[o].x + di.x, xb[o].y + di.y);
+      }
   }
 }
 
 // Chebyshev step: r -= A dp; dn = c1 dp + c2 D^-1 r; x += dn
 __global__ void cheb_step_kernel(Grid g, Sten s, const float* __restrict__ c,
-                                 const float* __restrict__ dinv, const float2* __restrict__ dp,
-                                 float2* dn, float2* r, float2* x, float c1, float c2,
+                                 const float* __restrict__ dinv, const float2* __restrict__ dpb,
+                                 float2* dnb, float2* rb, float2* xb, float c1, float c2, int F,
                                  const double* sc) {
-  if (sc[2] != 0.0) return;
+  int f0;
+  const unsigned act = chunk_active(F, sc, f0);
+  if (!act) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.total;
        i += (long long)gridDim.x * blockDim.x) {
     int ci[3];
     coords(g, i, ci);
-    const float2 a = sten_apply(g, s, c, dp, i, ci);
-    const float2 ri = make_float2(r[i].x - a.x, r[i].y - a.y);
+    float2 a[FC];
+    sten_apply_chunk(g, s, c, dpb, i, ci, f0, act, a);
     const float t = c2 * dinv[i];
-    const float2 di = make_float2(c1 * dp[i].x + t * ri.x, c1 * dp[i].y + t * ri.y);
-    r[i] = ri;
-    dn[i] = di;
-    x[i] = make_float2(x[i].x + di.x, x[i].y + di.y);
+#pragma unroll
+    for (int k = 0; k < FC; ++k)
+      if ((act >> k) & 1u) {
+        const long long o = (long long)(f0 + k) * g.total + i;
+        const float2 ri = make_float2(rb[o].x - a[k].x, rb[o].y - a[k].y);
+        const float2 dp = dpb[o];
+        const float2 di = make_float2(c1 * dp.x + t * ri.x, c1 * dp.y + t * ri.y);
+        rb[o] = ri;
+        dnb[o] = di;
+        xb[o] = make_float2(xb[o].x + di.x, xb[o].y + di.y);
+      }
   }
 }
 
 // r = b - A x
 __global__ void mg_resid_kernel(Grid g, Sten s, const float* __restrict__ c,
-                                const float2* __restrict__ b, const float2* __restrict__ x,
-                                float2* r, const double* sc) {
-  if (sc[2] != 0.0) return;
+                                const float2* __restrict__ bb, const float2* __restrict__ xb,
+                                float2* rb, int F, const double* sc) {
+  int f0;
+  const unsigned act = chunk_active(F, sc, f0);
+  if (!act) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.total;
        i += (long long)gridDim.x * blockDim.x) {
     int ci[3];
     coords(g, i, ci);
-    const float2 a = sten_apply(g, s, c, x, i, ci);
-    r[i] = make_float2(b[i].x - a.x, b[i].y - a.y);
+    float2 a[FC];
+    sten_apply_chunk(g, s, c, xb, i, ci, f0, act, a);
+#pragma unroll
+    for (int k = 0; k < FC; ++k)
+      if ((act >> k) & 1u) {
+        const long long o = (long long)(f0 + k) * g.total + i;
+        rb[o] = make_float2(bb[o].x - a[k].x, bb[o].y - a[k].y);
+      }
   }
 }
 
 // bc = P^T r
-__global__ void mg_restrict_kernel(Grid gf, Grid gc, const float2* __restrict__ r, float2* bc,
+__global__ void mg_restrict_kernel(Grid gf, Grid gc, const float2* __restrict__ rb, float2* bcb,
                                    const double* sc) {
-  if (sc[2] != 0.0) return;
+  const int f = blockIdx.y;
+  if (sc[f * NSC + 2] != 0.0) return;
+  const float2* r = rb + (long long)f * gf.total;
+  float2* bc = bcb + (long long)f * gc.total;
   for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < gc.total;
        I += (long long)gridDim.x * blockDim.x) {
     int CI[3];
@@ -616,9 +758,12 @@ __global__ void mg_restrict_kernel(Grid gf, Grid gc, const float2* __restrict__ 
 }
 
 // x += P xc
-__global__ void mg_prolong_kernel(Grid gf, Grid gc, const float2* __restrict__ xc, float2* x,
+__global__ void mg_prolong_kernel(Grid gf, Grid gc, const float2* __restrict__ xcb, float2* xb,
                                   const double* sc) {
-  if (sc[2] != 0.0) return;
+  const int f = blockIdx.y;
+  if (sc[f * NSC + 2] != 0.0) return;
+  const float2* xc = xcb + (long long)f * gc.total;
+  float2* x = xb + (long long)f * gf.total;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gf.total;
        i += (long long)gridDim.x * blockDim.x) {
     int ci[3];
@@ -640,16 +785,18 @@ __global__ void mg_prolong_kernel(Grid gf, Grid gc, const float2* __restrict__ x
   }
 }
 
-// Coarsest grid (at most COARSE_MAX nodes, one block of COARSE_MAX threads): COARSE_DEG
-// Chebyshev steps from x = 0 with the vectors in shared memory
+// Coarsest grid (at most COARSE_MAX nodes; one block of COARSE_MAX threads per field):
+// COARSE_DEG Chebyshev steps from x = 0 with the vectors in shared memory
 __global__ void __launch_bounds__(COARSE_MAX) mg_coarse_kernel(Grid g, Sten s,
                                                                const float* __restrict__ c,
                                                                const float* __restrict__ dinv,
-                                                               const float2* __restrict__ b,
-                                                               float2* x, double theta,
+                                                               const float2* __restrict__ bb,
+                                                               float2* xb, double theta,
                                                                double delta, const double* sc) {
-  if (sc[2] != 0.0) return;   // uniform over the block
+  const int f = blockIdx.x;
+  if (sc[f * NSC + 2] != 0.0) return;   // uniform over the block
   __shared__ float2 sd[2][COARSE_MAX];
+  const long long o = (long long)f * g.total;
   const int i = threadIdx.x;
   const bool on = i < g.total;
   int ci[3] = {0, 0, 0};
@@ -658,7 +805,7 @@ __global__ void __launch_bounds__(COARSE_MAX) mg_coarse_kernel(Grid g, Sten s,
   if (on) {
     coords(g, i, ci);
     di_inv = dinv[i];
-    ri = b[i];
+    ri = bb[o + i];
     const float t = di_inv * (float)(1.0 / theta);
     xi = make_float2(t * ri.x, t * ri.y);
     sd[0][i] = xi;
@@ -673,10 +820,10 @@ __global__ void __launch_bounds__(COARSE_MAX) mg_coarse_kernel(Grid g, Sten s,
     rho = rho_n;
     if (on) {
       float2 a = make_float2(0.f, 0.f);
-      for_offsets(s, [&](int o, int dx, int dy, int dz) {
+      for_offsets(s, [&](int oo, int dx, int dy, int dz) {
         const int xx = ci[0] + dx, yy = ci[1] + dy, zz = ci[2] + dz;
         if (xx < 0 || xx >= g.n[0] || yy < 0 || yy >= g.n[1] || zz < 0 || zz >= g.n[2]) return;
-        const float cv = c[(long long)o * g.total + i];
+        const float cv = c[(long long)oo * g.total + i];
         const float2 w = sd[cur][i + dx * g.stride[0] + dy * g.stride[1] + dz * g.stride[2]];
         a.x = fmaf(cv, w.x, a.x);
         a.y = fmaf(cv, w.y, a.y);
@@ -691,7 +838,39 @@ __global__ void __launch_bounds__(COARSE_MAX) mg_coarse_kernel(Grid g, Sten s,
     __syncthreads();
     cur ^= 1;
   }
-  if (on) x[i] = xi;
+  if (on) xb[o + i] = xi;
+}
+
+// Sensitivity maps (Eq. 1 as the paper applies it): the magnitude and the magnitude-normalised
+// map of every coil are smoothed as separate fields. Split S[l][c] into field c = |S| and field
+// C + c = S / |S| (0 where S = 0), each [L] in raster order.
+__global__ void sens_split_kernel(const float2* __restrict__ S, long long L, int C,
+                                  float2* fields) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < L * C;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long l = t / C;
+    const int c = (int)(t - l * C);
+    const float2 v = S[t];
+    const float m = hypotf(v.x, v.y);
+    fields[(long long)c * L + l] = make_float2(m, 0.f);
+    fields[(long long)(C + c) * L + l] =
+        m > 0.f ? make_float2(v.x / m, v.y / m) : make_float2(0.f, 0.f);
+  }
+}
+
+// Recombine: S[l][c] = m * u / |u| with m the smoothed magnitude (real part of field c) and u
+// the smoothed normalised map (field C + c); 0 where u = 0
+__global__ void sens_combine_kernel(const float2* __restrict__ fields, long long L, int C,
+                                    float2* S) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < L * C;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long l = t / C;
+    const int c = (int)(t - l * C);
+    const float m = fields[(long long)c * L + l].x;
+    const float2 u = fields[(long long)(C + c) * L + l];
+    const float a = hypotf(u.x, u.y);
+    S[t] = a > 0.f ? make_float2(m * u.x / a, m * u.y / a) : make_float2(0.f, 0.f);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -746,78 +925,70 @@ int grid_for(long long n, int sms) {
   return (int)std::max<long long>(1, std::min<long long>((n + VB - 1) / VB, 8LL * sms));
 }
 
-// V-cycle on level l: output in L[l].xo (or L[l].x on the coarsest level); returns that buffer
-float2* vcycle(std::vector<Level>& L, size_t l, const float2* b, const double* sc,
+// V-cycle on level l for F fields: output in L[l].xo (or L[l].x on the coarsest level);
+// returns that buffer
+float2* vcycle(std::vector<Level>& L, size_t l, const float2* b, int F, const double* sc,
                cudaStream_t st) {
   Level& v = L[l];
   if (l + 1 == L.size()) {
-    mg_coarse_kernel<<<1, COARSE_MAX, 0, st>>>(v.g, v.s, v.coef, v.dinv, b, v.x, v.theta, v.delta,
+    mg_coarse_kernel<<<F, COARSE_MAX, 0, st>>>(v.g, v.s, v.coef, v.dinv, b, v.x, v.theta, v.delta,
                                                sc);
     return v.x;
   }
+  const dim3 grid(v.grid, F);
+  const dim3 gridc(v.grid, (F + FC - 1) / FC);
   const float inv_theta = (float)(1.0 / v.theta);
   // pre-smoothing from x = 0
-  cheb_first0_kernel<<<v.grid, VB, 0, st>>>(v.g.total, v.dinv, b, v.x, v.r, v.d0, inv_theta, sc);
+  cheb_first0_kernel<<<grid, VB, 0, st>>>(v.g.total, v.dinv, b, v.x, v.r, v.d0, inv_theta, sc);
   float2 *dp = v.d0, *dn = v.d1;
   for (int k = 1; k < CHEB_DEG; ++k) {
-    cheb_step_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, dp, dn, v.r, v.x, v.c1[k],
-                                            v.c2[k], sc);
+    cheb_step_kernel<<<gridc, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, dp, dn, v.r, v.x, v.c1[k],
+                                           v.c2[k], F, sc);
     std::swap(dp, dn);
   }
   // coarse-grid correction
-  mg_resid_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, b, v.x, v.r, sc);
+  mg_resid_kernel<<<gridc, VB, 0, st>>>(v.g, v.s, v.coef, b, v.x, v.r, F, sc);
   Level& w = L[l + 1];
-  mg_restrict_kernel<<<w.grid, VB, 0, st>>>(v.g, w.g, v.r, w.b, sc);
-  const float2* xc = vcycle(L, l + 1, w.b, sc, st);
-  mg_prolong_kernel<<<v.grid, VB, 0, st>>>(v.g, w.g, xc, v.x, sc);
+  mg_restrict_kernel<<<dim3(w.grid, F), VB, 0, st>>>(v.g, w.g, v.r, w.b, sc);
+  const float2* xc = vcycle(L, l + 1, w.b, F, sc, st);
+  mg_prolong_kernel<<<grid, VB, 0, st>>>(v.g, w.g, xc, v.x, sc);
   // post-smoothing (the same polynomial) from the corrected x
-  cheb_first_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, b, v.x, v.xo, v.r, v.d0,
-                                           inv_theta, sc);
+  cheb_first_kernel<<<gridc, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, b, v.x, v.xo, v.r, v.d0,
+                                          inv_theta, F, sc);
   dp = v.d0;
   dn = v.d1;
   for (int k = 1; k < CHEB_DEG; ++k) {
-    cheb_step_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, dp, dn, v.r, v.xo, v.c1[k],
-                                            v.c2[k], sc);
+    cheb_step_kernel<<<gridc, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, dp, dn, v.r, v.xo,
+                                           v.c1[k], v.c2[k], F, sc);
     std::swap(dp, dn);
   }
   return v.xo;
 }
 
-}  // namespace
-}  // namespace sense
-
-using namespace sense;
-
-extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, const float* wd,
-                                const float* xhat, float* x, sense_smooth_info* info,
-                                void* stream) {
-  if (!o || !w0 || !wd || !xhat || !x) return set_error(SENSE_EINVAL, "null argument");
-  if (o->nx < 1 || o->ny < 1 || o->nz < 1 || (o->order != 1 && o->order != 2) ||
-      !(o->alpha >= 0.0) || o->max_iter < 0 || !(o->rel_tol >= 0.0) ||
-      (o->precond != SENSE_SMOOTH_PLAIN && o->precond != SENSE_SMOOTH_MULTIGRID))
-    return set_error(SENSE_EINVAL,
-                     "grid >= 1, order 1 or 2, alpha, max_iter, rel_tol >= 0, precond 0 or 1");
-  const void* ptrs[] = {w0, wd, xhat, x};
-  for (const void* p : ptrs)
-    if (!is_device_pointer(p)) return set_error(SENSE_EINVAL, "fields must be device memory");
-  cudaStream_t st = (cudaStream_t)stream;
+// Solve N x_f = w0^2 xhat_f for the F fields of xhat (field-major, F x n complex) into x.
+int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float* wd,
+                 const float2* XH, float2* X, sense_smooth_info* info, cudaStream_t st) {
   const Grid g = make_grid(o->nx, o->ny, o->nz);
   int dev = 0, sms = 1;
   SENSE_CUDA_TRY(cudaGetDevice(&dev));
   SENSE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = grid_for(g.total, sms);
+  const dim3 gridF(grid, F);
+  const dim3 gridC(grid, (F + FC - 1) / FC);
+  const long long pstride = 2LL * grid;
+  const long long nF = (long long)F * g.total;
   const bool mg = o->precond == SENSE_SMOOTH_MULTIGRID;
 
   Work W(st);
-  float2* r = W.get<float2>(g.total);
-  float2* p = W.get<float2>(g.total);
-  float2* q = W.get<float2>(g.total);
-  double* red = W.get<double>(grid * 2 + 8);
-  unsigned* counter = W.get<unsigned>(1);
-  if (!r || !p || !q || !red || !counter) return set_error(SENSE_ENOMEM, "smoothing workspace");
-  double* sc = red + grid * 2;   // [rr, bb, stop, step, beta, iters, rz, -]
-  float2* X = (float2*)x;
-  const float2* XH = (const float2*)xhat;
+  float2* r = W.get<float2>(nF);
+  float2* p = W.get<float2>(nF);
+  float2* q = W.get<float2>(nF);
+  double* part = W.get<double>((size_t)F * pstride);
+  unsigned* counter = W.get<unsigned>(F + 1);
+  double* sc = W.get<double>((size_t)F * NSC);
+  if (!r || !p || !q || !part || !counter || !sc)
+    return set_error(SENSE_ENOMEM, "smoothing workspace");
+  unsigned* nstop = counter + F;
   const float alpha = (float)o->alpha;
   const double tol2 = o->rel_tol * o->rel_tol;
   int rc = SENSE_OK;
@@ -825,19 +996,18 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
     const cudaError_t e = cudaGetLastError();
     if (rc == SENSE_OK && e != cudaSuccess) rc = cuda_error(e, what);
   };
-  if (cudaMemsetAsync(counter, 0, sizeof(unsigned), st) != cudaSuccess ||
-      cudaMemsetAsync(sc, 0, 8 * sizeof(double), st) != cudaSuccess ||
-      (X != XH && cudaMemcpyAsync(X, XH, (size_t)g.total * 8, cudaMemcpyDeviceToDevice, st) !=
-                      cudaSuccess))
+  if (cudaMemsetAsync(counter, 0, (F + 1) * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(sc, 0, (size_t)F * NSC * sizeof(double), st) != cudaSuccess ||
+      (X != XH &&
+       cudaMemcpyAsync(X, XH, (size_t)nF * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
     return cuda_error(cudaGetLastError(), "smoothing set-up");
 
   // ------------------------------------------------------------ multigrid hierarchy
   std::vector<Level> L;
   unsigned char* keep = nullptr;
-  float2* z = nullptr;
   if (mg) {
     keep = W.get<unsigned char>(g.total);
-    z = nullptr;
+    if (!keep) return set_error(SENSE_ENOMEM, "multigrid levels");
     Grid gl = g;
     int e0[3];
     for (int d = 0; d < 3; ++d) e0[d] = g.n[d] > 1 ? o->order : 0;
@@ -848,19 +1018,20 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
       v.s = sl;
       v.grid = grid_for(gl.total, sms);
       const bool coarsest = gl.total <= COARSE_MAX || (int)L.size() + 1 >= MAX_LEVELS;
+      const size_t nl = (size_t)F * gl.total;
       v.coef = W.get<float>((size_t)sl.count * gl.total);
       v.dinv = W.get<float>(gl.total);
-      v.x = W.get<float2>(gl.total);
-      if (!v.coef || !v.dinv || !v.x || !keep) return set_error(SENSE_ENOMEM, "multigrid levels");
+      v.x = W.get<float2>(nl);
+      if (!v.coef || !v.dinv || !v.x) return set_error(SENSE_ENOMEM, "multigrid levels");
       if (!coarsest) {
-        v.xo = W.get<float2>(gl.total);
-        v.r = W.get<float2>(gl.total);
-        v.d0 = W.get<float2>(gl.total);
-        v.d1 = W.get<float2>(gl.total);
+        v.xo = W.get<float2>(nl);
+        v.r = W.get<float2>(nl);
+        v.d0 = W.get<float2>(nl);
+        v.d1 = W.get<float2>(nl);
         if (!v.xo || !v.r || !v.d0 || !v.d1) return set_error(SENSE_ENOMEM, "multigrid levels");
       }
       if (!L.empty()) {
-        v.b = W.get<float2>(gl.total);
+        v.b = W.get<float2>(nl);
         if (!v.b) return set_error(SENSE_ENOMEM, "multigrid levels");
       }
       L.push_back(v);
@@ -875,7 +1046,7 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
       sl = make_box(ec);
     }
     if (gl.total > COARSE_MAX) return set_error(SENSE_EINVAL, "grid too large for the multigrid");
-    // operators
+    // operators (field-independent)
     unsigned* gmax = W.get<unsigned>(L.size());
     double* lam2 = W.get<double>(L.size());
     float2* pw = W.get<float2>(g.total);
@@ -885,23 +1056,20 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
       return cuda_error(cudaGetLastError(), "multigrid set-up");
     for (size_t l = 0; l < L.size() && rc == SENSE_OK; ++l) {
       Level& v = L[l];
+      if (cudaMemsetAsync(v.coef, 0, (size_t)v.s.count * v.g.total * sizeof(float), st) !=
+          cudaSuccess)
+        return cuda_error(cudaGetLastError(), "multigrid set-up");
       if (l == 0) {
-        if (cudaMemsetAsync(v.coef, 0, (size_t)v.s.count * v.g.total * sizeof(float), st) !=
-            cudaSuccess)
-          return cuda_error(cudaGetLastError(), "multigrid set-up");
         mg_fine_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, o->order, alpha, w0, wd, v.coef, keep);
       } else {
         const Level& f = L[l - 1];
-        if (cudaMemsetAsync(v.coef, 0, (size_t)v.s.count * v.g.total * sizeof(float), st) !=
-            cudaSuccess)
-          return cuda_error(cudaGetLastError(), "multigrid set-up");
         mg_galerkin_kernel<<<grid_for(v.g.total, sms), 128, 0, st>>>(f.g, f.s, f.coef, v.g, v.s,
                                                                      v.coef);
       }
       mg_diag_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, gmax + l);
       mg_vinit_kernel<<<v.grid, VB, 0, st>>>(pv, v.g.total);
       for (int k = 0; k < POWER_STEPS; ++k) {
-        mg_power_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, pv, pw, red, counter,
+        mg_power_kernel<<<v.grid, VB, 0, st>>>(v.g, v.s, v.coef, v.dinv, pv, pw, part, counter,
                                                lam2 + l);
         mg_normalize_kernel<<<v.grid, VB, 0, st>>>(pw, pv, v.g.total, lam2 + l);
       }
@@ -938,33 +1106,38 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
   }
 
   // ------------------------------------------------------------ CG start
-  smooth_apply_kernel<<<grid, VB, 0, st>>>(g, o->order, alpha, w0, wd, X, q, sc);
+  smooth_apply_kernel<<<gridC, VB, 0, st>>>(g, o->order, alpha, w0, wd, X, q, F, sc);
   chk("smooth apply");
-  smooth_init_kernel<<<grid, VB, 0, st>>>(w0, XH, q, g.total, r, p, red, counter, sc, tol2);
+  smooth_init_kernel<<<gridF, VB, 0, st>>>(w0, XH, q, g.total, r, p, part, pstride, counter, sc,
+                                           nstop, tol2);
   chk("smooth init");
   if (mg && rc == SENSE_OK) {
-    z = vcycle(L, 0, r, sc, st);
-    smooth_rz_kernel<<<grid, VB, 0, st>>>(z, r, keep, g.total, red, counter, sc, 1);
-    smooth_p_kernel<<<grid, VB, 0, st>>>(p, z, g.total, sc);
+    float2* z = vcycle(L, 0, r, F, sc, st);
+    smooth_rz_kernel<<<gridF, VB, 0, st>>>(z, r, keep, g.total, part, pstride, counter, sc,
+                                           nstop, 1);
+    smooth_p_kernel<<<gridF, VB, 0, st>>>(p, z, g.total, sc);
     chk("smooth preconditioner");
   }
   // one iteration, as a sequence of launches on stream s
   auto iteration = [&](cudaStream_t s) {
-    smooth_apply_kernel<<<grid, VB, 0, s>>>(g, o->order, alpha, w0, wd, p, q, sc);
-    smooth_pap_kernel<<<grid, VB, 0, s>>>(p, q, g.total, red, counter, sc, mg ? 6 : 0);
-    smooth_update_kernel<<<grid, VB, 0, s>>>(X, r, p, q, g.total, red, counter, sc, tol2);
+    smooth_apply_kernel<<<gridC, VB, 0, s>>>(g, o->order, alpha, w0, wd, p, q, F, sc);
+    smooth_pap_kernel<<<gridF, VB, 0, s>>>(p, q, g.total, part, pstride, counter, sc, nstop,
+                                           mg ? 6 : 0);
+    smooth_update_kernel<<<gridF, VB, 0, s>>>(X, r, p, q, g.total, part, pstride, counter, sc,
+                                              nstop, tol2);
     if (mg) {
-      float2* zz = vcycle(L, 0, r, sc, s);
-      smooth_rz_kernel<<<grid, VB, 0, s>>>(zz, r, keep, g.total, red, counter, sc, 0);
-      smooth_p_kernel<<<grid, VB, 0, s>>>(p, zz, g.total, sc);
+      float2* z = vcycle(L, 0, r, F, sc, s);
+      smooth_rz_kernel<<<gridF, VB, 0, s>>>(z, r, keep, g.total, part, pstride, counter, sc,
+                                            nstop, 0);
+      smooth_p_kernel<<<gridF, VB, 0, s>>>(p, z, g.total, sc);
     } else {
-      smooth_p_kernel<<<grid, VB, 0, s>>>(p, r, g.total, sc);
+      smooth_p_kernel<<<gridF, VB, 0, s>>>(p, r, g.total, sc);
     }
   };
 
   // ------------------------------------------------------------ iterations (graph replays)
   cudaGraphExec_t exec = nullptr;
-  double* hflag = nullptr;
+  unsigned* hstop = nullptr;
   cudaEvent_t ev = nullptr;
   if (rc == SENSE_OK && o->max_iter > 0) {
     cudaStream_t cs = nullptr;
@@ -986,10 +1159,10 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
       if (graph) cudaGraphDestroy(graph);
       cudaStreamDestroy(cs);
     }
-    if (rc == SENSE_OK && (cudaMallocHost((void**)&hflag, sizeof(double)) != cudaSuccess ||
+    if (rc == SENSE_OK && (cudaMallocHost((void**)&hstop, sizeof(unsigned)) != cudaSuccess ||
                            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess))
       rc = cuda_error(cudaGetLastError(), "smoothing poll buffers");
-    // replay in batches; the stop flag of batch k is read while batch k + 1 runs
+    // replay in batches; the stopped-field count of batch k is read while batch k + 1 runs
     bool pending = false;
     for (int done = 0; rc == SENSE_OK && done < o->max_iter;) {
       const int nb = std::min(POLL_EVERY, o->max_iter - done);
@@ -1003,9 +1176,9 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
           rc = cuda_error(cudaGetLastError(), "smoothing poll");
           break;
         }
-        if (*hflag != 0.0) break;
+        if (*hstop >= (unsigned)F) break;
       }
-      if (cudaMemcpyAsync(hflag, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+      if (cudaMemcpyAsync(hstop, nstop, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
               cudaSuccess ||
           cudaEventRecord(ev, st) != cudaSuccess) {
         rc = cuda_error(cudaGetLastError(), "smoothing poll");
@@ -1014,18 +1187,79 @@ extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, con
       pending = true;
     }
   }
-  double h[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<double> h((size_t)F * NSC, 0.0);
   if (rc == SENSE_OK &&
-      (cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      (cudaMemcpyAsync(h.data(), sc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess ||
        cudaStreamSynchronize(st) != cudaSuccess))
     rc = cuda_error(cudaGetLastError(), "smoothing result");
-  if (rc == SENSE_OK && info) {
-    info->iters = (int32_t)h[5];
-    info->rel_residual = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
-  }
+  if (rc == SENSE_OK && info)
+    for (int f = 0; f < F; ++f) {
+      const double* s = &h[(size_t)f * NSC];
+      info[f].iters = (int32_t)s[5];
+      info[f].rel_residual = s[1] > 0.0 ? std::sqrt(s[0] / s[1]) : 0.0;
+    }
   cudaStreamSynchronize(st);
   if (exec) cudaGraphExecDestroy(exec);
   if (ev) cudaEventDestroy(ev);
-  if (hflag) cudaFreeHost(hflag);
+  if (hstop) cudaFreeHost(hstop);
   return rc;
+}
+
+int check_opts(const sense_smooth_opts* o) {
+  if (o->nx < 1 || o->ny < 1 || o->nz < 1 || (o->order != 1 && o->order != 2) ||
+      !(o->alpha >= 0.0) || o->max_iter < 0 || !(o->rel_tol >= 0.0) || o->n_fields < 1 ||
+      o->n_fields > 65535 ||
+      (o->precond != SENSE_SMOOTH_PLAIN && o->precond != SENSE_SMOOTH_MULTIGRID))
+    return set_error(SENSE_EINVAL,
+                     "grid >= 1, order 1 or 2, alpha, max_iter, rel_tol >= 0, n_fields in "
+                     "[1, 65535], precond 0 or 1");
+  return SENSE_OK;
+}
+
+}  // namespace
+}  // namespace sense
+
+using namespace sense;
+
+extern "C" int sense_smooth_map(const sense_smooth_opts* o, const float* w0, const float* wd,
+                                const float* xhat, float* x, sense_smooth_info* info,
+                                void* stream) {
+  if (!o || !w0 || !wd || !xhat || !x) return set_error(SENSE_EINVAL, "null argument");
+  if (const int rc = check_opts(o)) return rc;
+  const void* ptrs[] = {w0, wd, xhat, x};
+  for (const void* p : ptrs)
+    if (!is_device_pointer(p)) return set_error(SENSE_EINVAL, "fields must be device memory");
+  return smooth_solve(o, o->n_fields, w0, wd, (const float2*)xhat, (float2*)x, info,
+                      (cudaStream_t)stream);
+}
+
+extern "C" int sense_smooth_sensitivities(const sense_smooth_opts* o, int32_t C, const float* w0,
+                                          const float* wd, const float* S_hat, float* S,
+                                          sense_smooth_info* info, void* stream) {
+  if (!o || !w0 || !wd || !S_hat || !S) return set_error(SENSE_EINVAL, "null argument");
+  if (C < 1 || 2LL * C > 65535) return set_error(SENSE_EINVAL, "coils in [1, 32767]");
+  sense_smooth_opts oo = *o;
+  oo.n_fields = 2 * C;
+  if (const int rc = check_opts(&oo)) return rc;
+  const void* ptrs[] = {w0, wd, S_hat, S};
+  for (const void* p : ptrs)
+    if (!is_device_pointer(p)) return set_error(SENSE_EINVAL, "maps must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long L = (long long)o->nx * o->ny * o->nz;
+  int dev = 0, sms = 1;
+  SENSE_CUDA_TRY(cudaGetDevice(&dev));
+  SENSE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  Work W(st);
+  float2* fields = W.get<float2>((size_t)2 * C * L);
+  if (!fields) return set_error(SENSE_ENOMEM, "sensitivity fields");
+  const int grid = grid_for(L * C, sms);
+  sens_split_kernel<<<grid, VB, 0, st>>>((const float2*)S_hat, L, C, fields);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  const int rc = smooth_solve(&oo, 2 * C, w0, wd, fields, fields, info, st);
+  if (rc != SENSE_OK) return rc;
+  sens_combine_kernel<<<grid, VB, 0, st>>>(fields, L, C, (float2*)S);
+  SENSE_CUDA_TRY(cudaGetLastError());
+  SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+  return SENSE_OK;
 }

@@ -34,7 +34,7 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
             "sense_batch_autotune", "sense_cg_solve_iterates", "sense_kspace_filter_mask",
             "sense_kspace_filter", "sense_plan_store_p", "sense_smooth_map",
-            "sense_kspace_filter_mask3d"]
+            "sense_kspace_filter_mask3d", "sense_smooth_sensitivities"]
 
 
 class SenseError(RuntimeError):
@@ -74,7 +74,7 @@ class SmoothOpts(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
-                ("precond", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("n_fields", ctypes.c_int32)]
 
 
 class SmoothInfo(ctypes.Structure):
@@ -109,6 +109,8 @@ def _load():
         "sense_plan_store_p": ([vp, i32, vp], ctypes.c_int),
         "sense_smooth_map": ([ctypes.POINTER(SmoothOpts), vp, vp, vp, vp,
                               ctypes.POINTER(SmoothInfo), vp], ctypes.c_int),
+        "sense_smooth_sensitivities": ([ctypes.POINTER(SmoothOpts), i32, vp, vp, vp, vp,
+                                        ctypes.POINTER(SmoothInfo), vp], ctypes.c_int),
         "sense_cg_solve_iterates": ([vp, vp, vp, ctypes.POINTER(CGOpts), vp,
                                      ctypes.POINTER(CGInfo), vp], ctypes.c_int),
         "sense_plan_profile": ([vp, ctypes.c_int], ctypes.c_int),
@@ -279,23 +281,55 @@ def sense_plan_store_p(plan, enable=True, stream=None):
 SMOOTH_PRECOND = {"none": 0, "multigrid": 1}
 
 
+def _smooth_opts(shape, order, alpha, max_iter, rel_tol, precond, n_fields):
+    nz, ny, nx = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
+    pc = SMOOTH_PRECOND[precond] if isinstance(precond, str) else int(precond)
+    return SmoothOpts(int(nx), int(ny), int(nz), int(order), float(alpha), int(max_iter),
+                      float(rel_tol), pc, int(n_fields))
+
+
 def sense_smooth_map(shape, order, alpha, w0, wd, xhat, x, max_iter=2000, rel_tol=1e-7,
                      precond="multigrid", stream=None):
     """Eq. 1 (order 2) / Eq. 3 (order 1) smoothing on a grid of `shape` ((ny, nx) or
-    (nz, ny, nx)); w0, wd float32 and xhat, x complex64 CUDA tensors; precond "multigrid"
-    (V-cycle preconditioned CG) or "none" (plain CG). Returns the info dict."""
-    nz, ny, nx = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
-    pc = SMOOTH_PRECOND[precond] if isinstance(precond, str) else int(precond)
-    o = SmoothOpts(int(nx), int(ny), int(nz), int(order), float(alpha), int(max_iter),
-                   float(rel_tol), pc)
-    info = SmoothInfo()
+    (nz, ny, nx)); w0, wd float32 and xhat, x complex64 CUDA tensors, [n] for one field or
+    [F][n] for F fields solved together; precond "multigrid" (V-cycle preconditioned CG) or
+    "none" (plain CG). Returns the info dict (one field) or a list of them."""
+    n = int(np.prod(shape))
+    F = 1 if xhat.ndim == 1 else int(xhat.shape[0])
+    if xhat.numel() != F * n or x.numel() != F * n:
+        raise ValueError("xhat and x must hold n_fields x prod(shape) values")
+    o = _smooth_opts(shape, order, alpha, max_iter, rel_tol, precond, F)
+    info = (SmoothInfo * F)()
     p0, _, s0 = _ptr(w0, np.float32)
     p1, _, _ = _ptr(wd, np.float32)
     p2, _, _ = _ptr(xhat)
     p3, _, _ = _ptr(x)
-    _check(_lib.sense_smooth_map(ctypes.byref(o), p0, p1, p2, p3, ctypes.byref(info),
+    _check(_lib.sense_smooth_map(ctypes.byref(o), p0, p1, p2, p3, info,
                                  _stream(s0, explicit=stream)), "sense_smooth_map")
-    return {"iters": info.iters, "rel_residual": info.rel_residual}
+    out = [{"iters": i.iters, "rel_residual": i.rel_residual} for i in info]
+    return out[0] if xhat.ndim == 1 else out
+
+
+def sense_smooth_sensitivities(shape, alpha, m_t, m_r, S_hat, S, max_iter=2000, rel_tol=1e-7,
+                               precond="multigrid", stream=None):
+    """Eq. 1 on every coil's sensitivity map: magnitude and magnitude-normalised map smoothed
+    separately (2 C fields in one solve) and recombined. m_t (trusted mask), m_r
+    (reconstruction mask): float32 [n]; S_hat, S: complex64 [n][C] CUDA tensors (may be the
+    same tensor). Returns the per-field info dicts (magnitudes first)."""
+    n = int(np.prod(shape))
+    C = int(S_hat.shape[-1])
+    if S_hat.numel() != n * C or S.numel() != n * C:
+        raise ValueError("S_hat and S must be [prod(shape)][C]")
+    o = _smooth_opts(shape, 2, alpha, max_iter, rel_tol, precond, 2 * C)
+    info = (SmoothInfo * (2 * C))()
+    p0, _, s0 = _ptr(m_t, np.float32)
+    p1, _, _ = _ptr(m_r, np.float32)
+    p2, _, _ = _ptr(S_hat)
+    p3, _, _ = _ptr(S)
+    _check(_lib.sense_smooth_sensitivities(ctypes.byref(o), C, p0, p1, p2, p3, info,
+                                           _stream(s0, explicit=stream)),
+           "sense_smooth_sensitivities")
+    return [{"iters": i.iters, "rel_residual": i.rel_residual} for i in info]
 
 
 def sense_kspace_filter_mask(nx, ny, dx, dy, kx, ky):

@@ -134,3 +134,61 @@ def test_unconstrained_voxels_keep_xhat_under_both_solvers():
         got = x.cpu().numpy().reshape(shape)
         assert np.array_equal(got[:5, :5], xhat[:5, :5])
         assert _rel(got.ravel(), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("precond", ["none", "multigrid"])
+def test_several_fields_in_one_solve(precond):
+    """Five right-hand sides on one grid (Eq. 1 masks): each field matches its own direct
+    solve, each stops on its own test, and the batch result equals five single-field calls."""
+    import torch
+    from paper_2604_09233_gb300 import native
+    dev = torch.device("cuda:0")
+    shape = (26, 22)
+    n = int(np.prod(shape))
+    _, m_t, m_r, _ = _fields(shape, 75)
+    rng = np.random.default_rng(76)
+    X = np.stack([_fields(shape, 80 + k)[0].ravel() * (1.0 + k) for k in range(4)] +
+                 [rng.normal(size=n) + 0j]).astype(np.complex64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out = torch.empty((5, n), dtype=torch.complex64, device=dev)
+    infos = native.sense_smooth_map(shape, 2, 0.5, t(m_t.ravel()), t(m_r.ravel()), t(X), out,
+                                    max_iter=20000, rel_tol=1e-7, precond=precond)
+    assert len(infos) == 5
+    for k in range(5):
+        ref = oracle.smooth_map(shape, 2, 0.5, m_t, m_r, X[k].astype(complex))
+        assert infos[k]["rel_residual"] <= 1e-7
+        assert _rel(out[k].cpu().numpy(), ref) <= 1e-4
+        one = torch.empty(n, dtype=torch.complex64, device=dev)
+        inf1 = native.sense_smooth_map(shape, 2, 0.5, t(m_t.ravel()), t(m_r.ravel()), t(X[k]),
+                                       one, max_iter=20000, rel_tol=1e-7, precond=precond)
+        assert inf1["iters"] == infos[k]["iters"]
+        assert _rel(out[k].cpu().numpy(), one.cpu().numpy()) <= 1e-6
+    print(precond, [i["iters"] for i in infos])
+
+
+@pytest.mark.parametrize("precond", ["none", "multigrid"])
+@pytest.mark.parametrize("shape", [(24, 20), (6, 10, 8)])
+def test_sensitivity_maps_match_oracle(shape, precond):
+    """sense_smooth_sensitivities (magnitude and normalised map of 4 coils, smoothed and
+    recombined on the device) against the oracle's per-coil direct solves; in place too."""
+    import torch
+    from paper_2604_09233_gb300 import native
+    dev = torch.device("cuda:0")
+    n = int(np.prod(shape))
+    _, m_t, m_r, _ = _fields(shape, 77)
+    S = np.stack([_fields(shape, 90 + c)[0].ravel() * np.exp(0.5j * c) for c in range(4)],
+                 axis=-1).astype(np.complex64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ref = oracle.smooth_sensitivities(shape, 0.5, m_t.ravel(), m_r.ravel(), S.astype(complex))
+    out = torch.empty((n, 4), dtype=torch.complex64, device=dev)
+    infos = native.sense_smooth_sensitivities(shape, 0.5, t(m_t.ravel()), t(m_r.ravel()), t(S),
+                                              out, max_iter=20000, rel_tol=1e-7,
+                                              precond=precond)
+    assert len(infos) == 8 and all(i["rel_residual"] <= 1e-7 for i in infos)
+    e = _rel(out.cpu().numpy(), ref)
+    print(f"sensitivities {shape} {precond}: {[i['iters'] for i in infos]}, vs oracle {e:.2e}")
+    assert e <= 1e-4
+    inplace = t(S)
+    native.sense_smooth_sensitivities(shape, 0.5, t(m_t.ravel()), t(m_r.ravel()), inplace,
+                                      inplace, max_iter=20000, rel_tol=1e-7, precond=precond)
+    assert _rel(inplace.cpu().numpy(), out.cpu().numpy()) <= 1e-6

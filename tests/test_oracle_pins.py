@@ -325,3 +325,33 @@ def test_smooth_map_weight_sits_on_the_row_voxel():
     expect = np.linalg.solve(N, xhat)
     got = oracle.smooth_map((1, 3), 1, 1.0, np.ones(3), np.array([1.0, 2.0, 5.0]), xhat)
     assert np.allclose(got, expect)
+
+
+def test_smooth_sensitivities_pins():
+    """Per-coil smoothing of magnitude and normalised map (Eq. 1 as the paper applies it):
+    a map with positive linear magnitude and constant phase, trusted on half the grid only, is
+    returned exactly over the whole grid (both parts lie in the null space of the second
+    difference); a unit-magnitude map with a curved phase keeps magnitude 1 everywhere (the
+    magnitude is processed on its own), while its phase is smoothed; coils are processed
+    independently (permuting coils permutes the result); an all-zero coil stays zero."""
+    ny, nx = 8, 10
+    y, x = np.mgrid[:ny, :nx]
+    half = (x < nx // 2).astype(float)
+    ones = np.ones((ny, nx))
+    exact = np.stack([(1.0 + 0.2 * x + 0.1 * y) * np.exp(0.7j),
+                      (2.0 + 0.05 * x - 0.1 * y) * np.exp(-2.1j)], axis=-1).reshape(-1, 2)
+    garbage = np.where(half.ravel()[:, None] > 0, exact, 9.0 - 4.0j)
+    out = oracle.smooth_sensitivities((ny, nx), 0.8, half, ones, garbage)
+    assert np.allclose(out, exact)
+    phase = np.exp(1j * 0.08 * (x - 4.5) ** 2).reshape(-1, 1)
+    rng = np.random.default_rng(3)
+    S = np.concatenate([phase, exact[:, :1], np.zeros((ny * nx, 1)),
+                        rng.normal(size=(ny * nx, 1)) + 1j * rng.normal(size=(ny * nx, 1))],
+                       axis=1)
+    out = oracle.smooth_sensitivities((ny, nx), 0.8, ones, ones, S)
+    assert np.allclose(np.abs(out[:, 0]), 1.0)
+    assert not np.allclose(out[:, 0], phase[:, 0], atol=1e-3)
+    assert np.array_equal(out[:, 2], np.zeros(ny * nx))
+    perm = [3, 0, 2, 1]
+    assert np.allclose(oracle.smooth_sensitivities((ny, nx), 0.8, ones, ones, S[:, perm]),
+                       out[:, perm])
