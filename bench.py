@@ -592,6 +592,16 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_apply_rate(wl)
         cb.pop("seconds")
+        # the same oracle on one host core (a smaller sample)
+        import oracle
+        n_threads = oracle.num_threads()
+        oracle.set_num_threads(1)
+        try:
+            one = oracle_apply_rate(wl, budget_s=4.0)
+        finally:
+            oracle.set_num_threads(n_threads)
+        cb["single_core"] = {"value": one["value"], "unit": UNIT, "cores": 1,
+                             "sample": one["sample"]}
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
