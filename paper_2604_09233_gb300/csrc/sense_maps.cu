@@ -796,6 +796,11 @@ __global__ void __launch_bounds__(COARSE_MAX) mg_coarse_kernel(Grid g, Sten s,
   const int f = blockIdx.x;
   if (sc[f * NSC + 2] != 0.0) return;   // uniform over the block
   __shared__ float2 sd[2][COARSE_MAX];
+  __shared__ float scoef[125 * COARSE_MAX];   // a box of half-width 2 in 3D at most
+  for (int k = threadIdx.x; k < s.count * COARSE_MAX; k += blockDim.x) {
+    const int oo = k / COARSE_MAX, ii = k - oo * COARSE_MAX;
+    scoef[k] = ii < g.total ? c[(long long)oo * g.total + ii] : 0.f;
+  }
   const long long o = (long long)f * g.total;
   const int i = threadIdx.x;
   const bool on = i < g.total;
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(COARSE_MAX) mg_coarse_kernel(Grid g, Sten s,
       for_offsets(s, [&](int oo, int dx, int dy, int dz) {
         const int xx = ci[0] + dx, yy = ci[1] + dy, zz = ci[2] + dz;
         if (xx < 0 || xx >= g.n[0] || yy < 0 || yy >= g.n[1] || zz < 0 || zz >= g.n[2]) return;
-        const float cv = c[(long long)oo * g.total + i];
+        const float cv = scoef[oo * COARSE_MAX + i];
         const float2 w = sd[cur][i + dx * g.stride[0] + dy * g.stride[1] + dz * g.stride[2]];
         a.x = fmaf(cv, w.x, a.x);
         a.y = fmaf(cv, w.y, a.y);
@@ -885,7 +890,8 @@ struct Level {
   float2 *b = nullptr, *x = nullptr, *xo = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr;
   double theta = 1.0, delta = 0.5;
   float c1[CHEB_DEG] = {}, c2[CHEB_DEG] = {};
-  int grid = 1;
+  int grid = 1;   // blocks of the single-field set-up kernels
+  dim3 gF, gC;    // grids of the per-field and the field-chunk kernels
 };
 
 // device buffers of one call, freed (after the stream's work) when the call returns
@@ -925,6 +931,14 @@ int grid_for(long long n, int sms) {
   return (int)std::max<long long>(1, std::min<long long>((n + VB - 1) / VB, 8LL * sms));
 }
 
+// grid of a kernel over `rows` fields (or field chunks) of n elements: about 8 blocks per SM in
+// all, each thread taking several elements when there are many fields
+dim3 grid_rows(long long n, int rows, int sms) {
+  const long long per = std::max<long long>(1, (8LL * sms + rows - 1) / rows);
+  return dim3((unsigned)std::max<long long>(1, std::min<long long>((n + VB - 1) / VB, per)),
+              (unsigned)rows);
+}
+
 // V-cycle on level l for F fields: output in L[l].xo (or L[l].x on the coarsest level);
 // returns that buffer
 float2* vcycle(std::vector<Level>& L, size_t l, const float2* b, int F, const double* sc,
@@ -935,8 +949,8 @@ float2* vcycle(std::vector<Level>& L, size_t l, const float2* b, int F, const do
                                                sc);
     return v.x;
   }
-  const dim3 grid(v.grid, F);
-  const dim3 gridc(v.grid, (F + FC - 1) / FC);
+  const dim3 grid = v.gF;
+  const dim3 gridc = v.gC;
   const float inv_theta = (float)(1.0 / v.theta);
   // pre-smoothing from x = 0
   cheb_first0_kernel<<<grid, VB, 0, st>>>(v.g.total, v.dinv, b, v.x, v.r, v.d0, inv_theta, sc);
@@ -949,7 +963,7 @@ float2* vcycle(std::vector<Level>& L, size_t l, const float2* b, int F, const do
   // coarse-grid correction
   mg_resid_kernel<<<gridc, VB, 0, st>>>(v.g, v.s, v.coef, b, v.x, v.r, F, sc);
   Level& w = L[l + 1];
-  mg_restrict_kernel<<<dim3(w.grid, F), VB, 0, st>>>(v.g, w.g, v.r, w.b, sc);
+  mg_restrict_kernel<<<w.gF, VB, 0, st>>>(v.g, w.g, v.r, w.b, sc);
   const float2* xc = vcycle(L, l + 1, w.b, F, sc, st);
   mg_prolong_kernel<<<grid, VB, 0, st>>>(v.g, w.g, xc, v.x, sc);
   // post-smoothing (the same polynomial) from the corrected x
@@ -973,8 +987,8 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
   SENSE_CUDA_TRY(cudaGetDevice(&dev));
   SENSE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = grid_for(g.total, sms);
-  const dim3 gridF(grid, F);
-  const dim3 gridC(grid, (F + FC - 1) / FC);
+  const dim3 gridF = grid_rows(g.total, F, sms);
+  const dim3 gridC = grid_rows(g.total, (F + FC - 1) / FC, sms);
   const long long pstride = 2LL * grid;
   const long long nF = (long long)F * g.total;
   const bool mg = o->precond == SENSE_SMOOTH_MULTIGRID;
@@ -1017,6 +1031,8 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
       v.g = gl;
       v.s = sl;
       v.grid = grid_for(gl.total, sms);
+      v.gF = grid_rows(gl.total, F, sms);
+      v.gC = grid_rows(gl.total, (F + FC - 1) / FC, sms);
       const bool coarsest = gl.total <= COARSE_MAX || (int)L.size() + 1 >= MAX_LEVELS;
       const size_t nl = (size_t)F * gl.total;
       v.coef = W.get<float>((size_t)sl.count * gl.total);
@@ -1045,7 +1061,8 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
       gl = make_grid(nc[0], nc[1], nc[2]);
       sl = make_box(ec);
     }
-    if (gl.total > COARSE_MAX) return set_error(SENSE_EINVAL, "grid too large for the multigrid");
+    if (gl.total > COARSE_MAX || L.back().s.count > 125)
+      return set_error(SENSE_EINVAL, "grid too large for the multigrid");
     // operators (field-independent)
     unsigned* gmax = W.get<unsigned>(L.size());
     double* lam2 = W.get<double>(L.size());
