@@ -131,3 +131,38 @@ def test_batch_create_without_gpu_reports_no_device():
         native.sense_batch_create([(np.zeros((4, 1)), np.zeros((1, 5)),
                                     np.zeros((5, 2), np.complex64), None)])
     assert e.value.code == -7
+
+
+def test_smoothing_and_filter_entry_points_check_arguments_first():
+    """Map smoothing rejects null pointers, impossible grids, orders, field counts and
+    preconditioner codes, and host memory, before any device work; the k-space filter mask
+    rejects empty grids."""
+    from paper_2604_09233_gb300 import native
+    lib = native._lib
+    buf = (ctypes.c_float * 64)()
+    info = (native.SmoothInfo * 4)()
+
+    def opts(**kw):
+        base = dict(nx=4, ny=4, nz=1, order=2, alpha=0.5, max_iter=10, rel_tol=1e-6, precond=1,
+                    n_fields=1)
+        base.update(kw)
+        return native.SmoothOpts(*[base[k] for k in ("nx", "ny", "nz", "order", "alpha",
+                                                     "max_iter", "rel_tol", "precond",
+                                                     "n_fields")])
+
+    for bad in (dict(nx=0), dict(order=3), dict(alpha=-1.0), dict(max_iter=-1),
+                dict(rel_tol=-1e-3), dict(precond=2), dict(n_fields=0), dict(n_fields=70000)):
+        o = opts(**bad)
+        assert lib.sense_smooth_map(ctypes.byref(o), buf, buf, buf, buf, info, None) == -1, bad
+    o = opts()
+    assert lib.sense_smooth_map(None, buf, buf, buf, buf, info, None) == -1
+    assert lib.sense_smooth_map(ctypes.byref(o), None, buf, buf, buf, info, None) == -1
+    # host arrays are refused (the solver works on device fields only)
+    assert lib.sense_smooth_map(ctypes.byref(o), buf, buf, buf, buf, info, None) == -1
+    assert b"device" in lib.sense_last_error()
+    assert lib.sense_smooth_sensitivities(ctypes.byref(o), 0, buf, buf, buf, buf, info,
+                                          None) == -1
+    assert lib.sense_smooth_sensitivities(ctypes.byref(o), 40000, buf, buf, buf, buf, info,
+                                          None) == -1
+    kx = (ctypes.c_double * 3)(0.0, 1.0, 0.0)
+    assert lib.sense_kspace_filter_mask(0, 4, 1e-3, 1e-3, kx, kx, 3, buf) == -1
