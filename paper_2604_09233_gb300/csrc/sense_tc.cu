@@ -503,8 +503,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     // phase in turns -> radians; the E^H pass generates the conjugate tile
     const float2 ang_scale = MODE == ADJ ? make_float2(-6.283185307179586f, -6.283185307179586f)
                                          : make_float2(6.283185307179586f, 6.283185307179586f);
-    const float2 RND = make_float2(12582912.f, 12582912.f);    // 1.5 * 2^23: round to integer
-    const float2 NRND = make_float2(-12582912.f, -12582912.f);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     float own[RT];
     // per-thread running sum of the run, in shared memory (frees registers for the
@@ -703,10 +701,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              // reduce to [-1/2, 1/2] turn: t - rint(t); then radians (sign: conjugate
-              // tile for the E^H pass)
-              const float2 tr = __ffma2_rn(__fadd2_rn(__fadd2_rn(t[k], RND), NRND), NEG1, t[k]);
-              const float2 ang = __fmul2_rn(tr, ang_scale);
+              // radians (sign: conjugate tile for the E^H pass). No range reduction: |A|,
+              // |B| <= 1/2 turn, so |theta| <= 1 + |D| turns, and the argument error the
+              // sine unit adds for it, about |theta| 2^-24 turn, is of the order of the FP32
+              // rounding D already carries and of the unit's own error
+              const float2 ang = __fmul2_rn(t[k], ang_scale);
               float2 cs, sn;
               __sincosf(ang.x, &sn.x, &cs.x);
               __sincosf(ang.y, &sn.y, &cs.y);
@@ -1210,7 +1209,6 @@ __global__ void __launch_bounds__(128) gen_stored_kernel(InstDesc d, int RT, lon
   __shared__ float s_anc[128];
   const int row = threadIdx.x;
   const float ang_scale = MODE == ADJ ? -6.283185307179586f : 6.283185307179586f;
-  const float RND = 12582912.f;
   for (long long w = blockIdx.x; w < W; w += gridDim.x) {
     const int o = (int)(w / d.n_inner), in = (int)(w % d.n_inner);
     __syncthreads();
@@ -1231,8 +1229,7 @@ __global__ void __launch_bounds__(128) gen_stored_kernel(InstDesc d, int RT, lon
           const int v = v0 + 2 * k + e;
           float t = __fadd_rn(s_anc[v], rb);
           for (int q = 0; q < RT; ++q) t = __fmaf_rn(own[q], s_col[q * 128 + v], t);
-          const float tr = __fmaf_rn(__fadd_rn(__fadd_rn(t, RND), -RND), -1.0f, t);
-          const float ang = __fmul_rn(tr, ang_scale);
+          const float ang = __fmul_rn(t, ang_scale);
           __sincosf(ang, &sn[e], &cs[e]);
         }
         const float2 hc = hi11(make_float2(cs[0], cs[1])), hs = hi11(make_float2(sn[0], sn[1]));
