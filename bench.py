@@ -258,12 +258,12 @@ def run_reference(args):
 # from one ncu capture, profiles/tc_pass_2d256_32coil_sh3.md), keyed by the SHA-256 of the
 # pass-kernel source they were taken on (pass_kernel_source_hash); any other source reports null.
 KERNEL_TRAFFIC = {
-    "3faf7cb8a46440bd0d3c1642430adbae4341ce8bc1237890b183e9490b8e8fdf": {
+    "9d6b40d3d0513d3e2a084353fece0b2b71af22771ff8bfab8d40f4eadb118811": {
         "workload": "2d_256x256_32coil_35750samp_sh3", "precision": "tc_split",
-        "tc_encode_pass": 169214464 + 8960256,
-        "tc_adjoint_pass": 182843392 + 798976,
-        "stored_tc_encode_pass": 19579746816 + 12485376,
-        "stored_tc_adjoint_pass": 19522087424 + 686080,
+        "tc_encode_pass": 168462080 + 9367040,
+        "tc_adjoint_pass": 182305536 + 378112,
+        "stored_tc_encode_pass": 19522951680 + 12660992,
+        "stored_tc_adjoint_pass": 19492078592 + 681216,
     },
 }
 
