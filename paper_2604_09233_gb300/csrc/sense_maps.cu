@@ -989,7 +989,9 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
   const int grid = grid_for(g.total, sms);
   const dim3 gridF = grid_rows(g.total, F, sms);
   const dim3 gridC = grid_rows(g.total, (F + FC - 1) / FC, sms);
-  const long long pstride = 2LL * grid;
+  // partial sums: 2 per block of each field's reduction kernels (gridF.x blocks); the
+  // single-field set-up kernels of the hierarchy use field 0's region with up to `grid` blocks
+  const long long pstride = 2LL * gridF.x;
   const long long nF = (long long)F * g.total;
   const bool mg = o->precond == SENSE_SMOOTH_MULTIGRID;
 
@@ -997,7 +999,7 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
   float2* r = W.get<float2>(nF);
   float2* p = W.get<float2>(nF);
   float2* q = W.get<float2>(nF);
-  double* part = W.get<double>((size_t)F * pstride);
+  double* part = W.get<double>((size_t)std::max<long long>(F * pstride, 2LL * grid));
   unsigned* counter = W.get<unsigned>(F + 1);
   double* sc = W.get<double>((size_t)F * NSC);
   if (!r || !p || !q || !part || !counter || !sc)
