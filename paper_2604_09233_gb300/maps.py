@@ -1,5 +1,5 @@
 """Sensitivity and B0 map smoothing (Eqs. 1 and 3) on synthetic maps: masks and a command-line
-driver that times the device solves.
+tool that times the device solves.
 
 The paper derives its masks from prescan data: the trusted mask M_T (voxels with enough signal)
 and the reconstruction mask M_R (every voxel that may hold signal, a slightly dilated head

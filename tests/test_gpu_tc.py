@@ -115,7 +115,7 @@ def test_tc_results_are_deterministic(case):
 @pytest.mark.parametrize("matrix,n_samples", [(20, 1000), (12, 300), (40, 5000)])
 def test_tc_no_reads_of_unwritten_device_memory(matrix, n_samples):
     """Freshly allocated device memory is poisoned with NaN first (allocate, fill, hand back
-    to the driver), so any read of a workspace element that no kernel wrote shows up. Small
+    to the CUDA allocator), so any read of a workspace element that no kernel wrote shows up. Small
     problems (fewer block pairs than SMs) once summed partial slots of CTAs with no work."""
     import torch
     from paper_2604_09233_gb300 import native

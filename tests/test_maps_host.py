@@ -1,4 +1,4 @@
-"""Host helpers of the map-smoothing driver: the synthetic masks are nested (the trusted mask
+"""Host helpers of the map-smoothing command-line tool: the synthetic masks are nested (the trusted mask
 inside the reconstruction mask), grow with the dilation, and match a direct construction."""
 import numpy as np
 
