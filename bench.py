@@ -264,6 +264,9 @@ KERNEL_TRAFFIC = {
         "tc_adjoint_pass": 182305536 + 378112,
         "stored_tc_encode_pass": 19522951680 + 12660992,
         "stored_tc_adjoint_pass": 19492078592 + 681216,
+        # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
+        "inst_tc_encode_pass": 2459430132,
+        "inst_tc_adjoint_pass": 2519748336,
     },
 }
 
@@ -562,6 +565,20 @@ def run_ours(args):
               "frac": tflops / peak_tc, "traffic": traffic, "kernel": kc,
               "peak_source": f"bf16 sustained, {peak_kind} (fp16 = bf16 rate)"}
     roof = sfu if sfu["frac"] >= tensor["frac"] else tensor
+    # the pass is bound by instruction issue in its generator warps: warp instructions per
+    # second against one per clock per SM sub-partition
+    clocks = clk.summary()
+    inst = _kernel_traffic(wl.name, prec_name, "inst_" + kc)
+    issue = None
+    if inst is not None:
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_issue = 4.0 * n_sm * mhz * 1e6
+        issue = {"bound": "issue", "achieved": inst / t_launch / 1e9,
+                 "peak": peak_issue / 1e9, "unit": "Gwarp-inst/s",
+                 "frac": inst / t_launch / peak_issue, "kernel": kc, "inst_per_launch": inst,
+                 "peak_source": "4 warp instructions per clock per SM at the median sampled SM "
+                                "clock; instructions per launch from ncu for this kernel code"}
 
     vsc = 2.0 * wl.L * wl.K * wl.C
     line = {
@@ -575,8 +592,9 @@ def run_ours(args):
         "cg_rel_err_vs_fp32_path": err_vs_fp32,
         "roofline": roof,
         "roofline_other": tensor if roof is sfu else sfu,
+        "roofline_issue": issue,
         "kernel_ms": {k: stats[k]["ms"] for k in native.KERNEL_CLASSES},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": wl.K * wl.C * 8,
                 "d2h_bytes_per_step": wl.L * 8},
         "gpu_launches": stats["launches"],
@@ -719,7 +737,7 @@ def run_batch(args):
                      "unit": "Gsincos/s", "frac": achieved / sincos_peak, "traffic": None,
                      "kernel": "batched E^H E (two persistent passes + per-instance kernels)",
                      "peak_source": "measured on this GPU by sense_diag_sincos_rate"},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(w.K * w.C * 8 for w in wls)),
                 "d2h_bytes_per_step": int(sum(w.L * 8 for w in wls))},
