@@ -40,6 +40,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "sense_internal.cuh"
@@ -894,19 +896,49 @@ struct Level {
   dim3 gF, gC;    // grids of the per-field and the field-chunk kernels
 };
 
-// device buffers of one call, freed (after the stream's work) when the call returns
+// Workspace comes from a stream-ordered memory pool of the library's own (one per device),
+// which keeps up to 1 GiB of freed blocks for the next call: repeated solves then allocate in
+// microseconds instead of one cudaMalloc per buffer.
+cudaMemPool_t work_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = 1ull << 30;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
+// device buffers of one call, allocated and freed in stream order on the call's stream
 struct Work {
   cudaStream_t st;
+  cudaMemPool_t pool = nullptr;
   std::vector<void*> bufs;
-  explicit Work(cudaStream_t s) : st(s) {}
+  explicit Work(cudaStream_t s) : st(s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) pool = work_pool(dev);
+  }
   ~Work() {
-    cudaStreamSynchronize(st);
-    for (void* p : bufs) cudaFree(p);
+    for (void* p : bufs) cudaFreeAsync(p, st);
   }
   template <class T>
   T* get(size_t count) {
     void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    if (!pool ||
+        cudaMallocFromPoolAsync(&p, std::max<size_t>(count, 1) * sizeof(T), pool, st) !=
+            cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -914,6 +946,16 @@ struct Work {
     return (T*)p;
   }
 };
+
+// pinned word the host polls the stopped-field count into (one per host thread, kept)
+unsigned* poll_word() {
+  thread_local unsigned* w = nullptr;
+  if (!w && cudaMallocHost((void**)&w, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    w = nullptr;
+  }
+  return w;
+}
 
 Grid make_grid(int nx, int ny, int nz) {
   Grid g;
@@ -1178,8 +1220,9 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
       if (graph) cudaGraphDestroy(graph);
       cudaStreamDestroy(cs);
     }
-    if (rc == SENSE_OK && (cudaMallocHost((void**)&hstop, sizeof(unsigned)) != cudaSuccess ||
-                           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess))
+    hstop = poll_word();
+    if (rc == SENSE_OK && (!hstop || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) !=
+                                         cudaSuccess))
       rc = cuda_error(cudaGetLastError(), "smoothing poll buffers");
     // replay in batches; the stopped-field count of batch k is read while batch k + 1 runs
     bool pending = false;
@@ -1221,7 +1264,6 @@ int smooth_solve(const sense_smooth_opts* o, int F, const float* w0, const float
   cudaStreamSynchronize(st);
   if (exec) cudaGraphExecDestroy(exec);
   if (ev) cudaEventDestroy(ev);
-  if (hstop) cudaFreeHost(hstop);
   return rc;
 }
 
