@@ -950,7 +950,7 @@ struct Work {
 // pinned word the host polls the stopped-field count into (one per host thread, kept)
 unsigned* poll_word() {
   thread_local unsigned* w = nullptr;
-  if (!w && cudaMallocHost((void**)&w, sizeof(unsigned)) != cudaSuccess) {
+  if (!w && cudaHostAlloc((void**)&w, sizeof(unsigned), cudaHostAllocPortable) != cudaSuccess) {
     cudaGetLastError();
     w = nullptr;
   }
