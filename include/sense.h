@@ -257,7 +257,9 @@ int sense_kspace_filter(int32_t nx, int32_t ny, int32_t nz, const float* mask, f
  * interpolation, Chebyshev smoothing on the diagonal; built on the device at every call; the
  * paper's incomplete-Cholesky choice is sequential and is not offered). info (nullable):
  * [n_fields] host entries, iterations run and the final relative residual of the normal
- * equations per field. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+ * equations per field. Workspace (about 10 field-sized vectors plus the hierarchy) comes from a
+ * stream-ordered memory pool the library keeps per device, which retains up to 1 GiB of freed
+ * blocks between calls. Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
 #define SENSE_SMOOTH_PLAIN 0
 #define SENSE_SMOOTH_MULTIGRID 1
 typedef struct {
