@@ -1,0 +1,43 @@
+"""Host logic of bench.py that needs no GPU: the pass-kernel code hash that keys the ncu
+traffic table ignores comments and blank lines but not code, and the traffic lookup answers
+only for the captured workload and precision."""
+import os
+import shutil
+
+import bench
+
+
+def _copy_sources(tmp_path):
+    src = os.path.join(bench.ROOT, "paper_2604_09233_gb300", "csrc")
+    dst = tmp_path / "paper_2604_09233_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for name in ("sense_tc.cu", "sense_tc.cuh"):
+        shutil.copy(os.path.join(src, name), dst / name)
+    return dst
+
+
+def test_pass_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    dst = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.pass_kernel_source_hash()
+    f = dst / "sense_tc.cu"
+    text = f.read_text()
+    anchor = "__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {"
+    assert anchor in text
+    f.write_text(text.replace(anchor, "// an added comment\n\n" + anchor + "  // trailing"))
+    assert bench.pass_kernel_source_hash() == h0
+    f.write_text(text.replace("6.283185307179586f", "6.2831853f", 1))
+    assert bench.pass_kernel_source_hash() != h0
+
+
+def test_traffic_lookup_is_specific_to_the_captured_case():
+    rec = bench.KERNEL_TRAFFIC.get(bench.pass_kernel_source_hash())
+    if rec is None:
+        # the kernel changed since the last capture: every lookup reports no traffic
+        assert bench._kernel_traffic("2d_256x256_32coil_35750samp_sh3", "tc_split",
+                                     "tc_adjoint_pass") is None
+        return
+    wl, prec = rec["workload"], rec["precision"]
+    assert bench._kernel_traffic(wl, prec, "tc_adjoint_pass") == rec["tc_adjoint_pass"]
+    assert bench._kernel_traffic(wl, "tc_fp16", "tc_adjoint_pass") is None
+    assert bench._kernel_traffic("another_workload", prec, "tc_adjoint_pass") is None
