@@ -166,3 +166,18 @@ def test_smoothing_and_filter_entry_points_check_arguments_first():
                                           None) == -1
     kx = (ctypes.c_double * 3)(0.0, 1.0, 0.0)
     assert lib.sense_kspace_filter_mask(0, 4, 1e-3, 1e-3, kx, kx, 3, buf) == -1
+
+
+def test_header_is_plain_c():
+    """include/sense.h compiles as C99 and as C++17 on its own (plain C types only)."""
+    import shutil
+    import subprocess
+    from paper_2604_09233_gb300 import build
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(build.__file__))),
+                       "include", "sense.h")
+    for cc, std, lang in (("gcc", "-std=c99", "c"), ("g++", "-std=c++17", "c++")):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not available")
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", lang,
+                            hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
