@@ -259,14 +259,23 @@ def run_reference(args):
 # pass-kernel source they were taken on (pass_kernel_source_hash); any other source reports null.
 KERNEL_TRAFFIC = {
     "9d6b40d3d0513d3e2a084353fece0b2b71af22771ff8bfab8d40f4eadb118811": {
-        "workload": "2d_256x256_32coil_35750samp_sh3", "precision": "tc_split",
-        "tc_encode_pass": 168462080 + 9367040,
-        "tc_adjoint_pass": 182305536 + 378112,
-        "stored_tc_encode_pass": 19522951680 + 12660992,
-        "stored_tc_adjoint_pass": 19492078592 + 681216,
-        # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
-        "inst_tc_encode_pass": 2459430132,
-        "inst_tc_adjoint_pass": 2519748336,
+        "2d_256x256_32coil_35750samp_sh3": {
+            "precision": "tc_split",
+            "tc_encode_pass": 168462080 + 9367040,
+            "tc_adjoint_pass": 182305536 + 378112,
+            "stored_tc_encode_pass": 19522951680 + 12660992,
+            "stored_tc_adjoint_pass": 19492078592 + 681216,
+            # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
+            "inst_tc_encode_pass": 2459430132,
+            "inst_tc_adjoint_pass": 2519748336,
+        },
+        "3d_96x96x48_32coil_62400samp_sh2": {
+            "precision": "tc_split",
+            "tc_encode_pass": 11170881536 + 21115392,
+            "tc_adjoint_pass": 1890571520 + 4946432,
+            "inst_tc_encode_pass": 28915454995,
+            "inst_tc_adjoint_pass": 29616864412,
+        },
     },
 }
 
@@ -293,8 +302,8 @@ def pass_kernel_source_hash():
 
 
 def _kernel_traffic(workload, prec_name, kernel):
-    rec = KERNEL_TRAFFIC.get(pass_kernel_source_hash())
-    if not rec or rec["workload"] != workload or rec["precision"] != prec_name:
+    rec = KERNEL_TRAFFIC.get(pass_kernel_source_hash(), {}).get(workload)
+    if not rec or rec["precision"] != prec_name:
         return None
     return rec.get(kernel)
 

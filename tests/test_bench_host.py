@@ -31,13 +31,14 @@ def test_pass_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
 
 
 def test_traffic_lookup_is_specific_to_the_captured_case():
-    rec = bench.KERNEL_TRAFFIC.get(bench.pass_kernel_source_hash())
-    if rec is None:
+    recs = bench.KERNEL_TRAFFIC.get(bench.pass_kernel_source_hash())
+    if recs is None:
         # the kernel changed since the last capture: every lookup reports no traffic
         assert bench._kernel_traffic("2d_256x256_32coil_35750samp_sh3", "tc_split",
                                      "tc_adjoint_pass") is None
         return
-    wl, prec = rec["workload"], rec["precision"]
-    assert bench._kernel_traffic(wl, prec, "tc_adjoint_pass") == rec["tc_adjoint_pass"]
-    assert bench._kernel_traffic(wl, "tc_fp16", "tc_adjoint_pass") is None
-    assert bench._kernel_traffic("another_workload", prec, "tc_adjoint_pass") is None
+    for wl, rec in recs.items():
+        prec = rec["precision"]
+        assert bench._kernel_traffic(wl, prec, "tc_adjoint_pass") == rec["tc_adjoint_pass"]
+        assert bench._kernel_traffic(wl, "tc_fp16", "tc_adjoint_pass") is None
+    assert bench._kernel_traffic("another_workload", "tc_split", "tc_adjoint_pass") is None
