@@ -7,18 +7,19 @@ import shutil
 import bench
 
 
-def _copy_sources(tmp_path):
+def _copy_sources(root):
+    import pathlib
     src = os.path.join(bench.ROOT, "paper_2604_09233_gb300", "csrc")
-    dst = tmp_path / "paper_2604_09233_gb300" / "csrc"
+    dst = pathlib.Path(root) / "paper_2604_09233_gb300" / "csrc"
     dst.mkdir(parents=True)
     for name in ("sense_tc.cu", "sense_tc.cuh"):
         shutil.copy(os.path.join(src, name), dst / name)
     return dst
 
 
-def test_pass_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
-    dst = _copy_sources(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+def test_pass_kernel_hash_ignores_comments_but_not_code(repo_tmp, monkeypatch):
+    dst = _copy_sources(repo_tmp)
+    monkeypatch.setattr(bench, "ROOT", str(repo_tmp))
     h0 = bench.pass_kernel_source_hash()
     f = dst / "sense_tc.cu"
     text = f.read_text()

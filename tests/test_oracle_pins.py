@@ -239,18 +239,26 @@ def test_grad_omega_adjoint_matches_central_differences(small):
         assert abs(fd - grad[l]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max()), l
 
 
-def test_lcurve_corner_on_parabola_vertex():
+def lcurve_pins(lcurve_corner):
     """(a, b) = (x, x^2) traversed right to left: curvature peaks (value 2) at the vertex."""
     xs = np.linspace(2.0, -1.0, 31)           # vertex at index 20
-    idx = oracle.lcurve_corner(np.exp(xs), np.exp(xs ** 2))
+    idx = lcurve_corner(np.exp(xs), np.exp(xs ** 2))
     assert idx == 20
     # a shifted vertex moves the corner with it
     xs2 = xs + 0.5                             # vertex now where xs == -0.5 -> index 25
-    assert oracle.lcurve_corner(np.exp(xs2), np.exp((xs2 - 0.0) ** 2)) == 25
-    assert oracle.lcurve_corner([1.0, 2.0], [1.0, 1.0]) == -1
+    assert lcurve_corner(np.exp(xs2), np.exp((xs2 - 0.0) ** 2)) == 25
+    assert lcurve_corner([1.0, 2.0], [1.0, 1.0]) == -1
+
+
+def test_lcurve_corner_on_parabola_vertex():
+    lcurve_pins(oracle.lcurve_corner)
 
 
 def test_kspace_filter_keeps_inside_and_removes_outside_plane_waves():
+    kspace_filter_pins(oracle.kspace_filter)
+
+
+def kspace_filter_pins(kspace_filter):
     """A Cartesian plane wave rho(x) = e^{-i k_u r_x} has all of its k-space content at k_u:
     the filter returns it unchanged when f(u) = 1 and removes it when f(u) = 0; f = 1 is the
     identity; the transform is linear (checked on a sum)."""
@@ -265,15 +273,15 @@ def test_kspace_filter_keeps_inside_and_removes_outside_plane_waves():
                                      + (v - ny // 2) * (y - ny // 2) / ny)).ravel()
 
     a, b = wave(7, 2), wave(3, 4)
-    assert np.allclose(oracle.kspace_filter(a, shape, f), a, atol=1e-12)
-    assert np.allclose(oracle.kspace_filter(b, shape, f), 0, atol=1e-12)
-    assert np.allclose(oracle.kspace_filter(2 * a + b, shape, f), 2 * a, atol=1e-12)
+    assert np.allclose(kspace_filter(a, shape, f), a, atol=1e-12)
+    assert np.allclose(kspace_filter(b, shape, f), 0, atol=1e-12)
+    assert np.allclose(kspace_filter(2 * a + b, shape, f), 2 * a, atol=1e-12)
     rng = np.random.default_rng(6)
     z = rng.normal(size=60) + 1j * rng.normal(size=60)
-    assert np.allclose(oracle.kspace_filter(z, shape, np.ones(shape)), z, atol=1e-12)
+    assert np.allclose(kspace_filter(z, shape, np.ones(shape)), z, atol=1e-12)
     # 3D: the same along the third axis
     z3 = rng.normal(size=(3, 4, 5)) + 1j * rng.normal(size=(3, 4, 5))
-    assert np.allclose(oracle.kspace_filter(z3, (3, 4, 5), np.ones((3, 4, 5))), z3.ravel())
+    assert np.allclose(kspace_filter(z3, (3, 4, 5), np.ones((3, 4, 5))), z3.ravel())
 
 
 def test_kspace_mask_of_a_square_of_samples():
@@ -290,6 +298,10 @@ def test_kspace_mask_of_a_square_of_samples():
 
 
 def test_smooth_map_pins():
+    smooth_map_pins(oracle.smooth_map)
+
+
+def smooth_map_pins(smooth_map):
     """Eq. 1 / Eq. 3 smoothing: a field in the null space of the derivative is returned unchanged
     for any alpha (linear for second differences, constant for first differences); with the
     data term on half the grid only (Eq. 1 with M_T a half, M_R everything) a linear field is
@@ -299,35 +311,66 @@ def test_smooth_map_pins():
     y, x = np.mgrid[:ny, :nx]
     lin = (0.3 + 0.2j) * x - (0.1 - 0.4j) * y + 1.0
     ones = np.ones((ny, nx))
-    assert np.allclose(oracle.smooth_map((ny, nx), 2, 5.0, ones, ones, lin), lin.ravel())
+    assert np.allclose(smooth_map((ny, nx), 2, 5.0, ones, ones, lin), lin.ravel())
     const = np.full((ny, nx), 2.0 - 1.0j)
     rng = np.random.default_rng(7)
     eps = rng.uniform(0.5, 2.0, size=(ny, nx))
-    assert np.allclose(oracle.smooth_map((ny, nx), 1, 3.0, ones, eps, const), const.ravel())
+    assert np.allclose(smooth_map((ny, nx), 1, 3.0, ones, eps, const), const.ravel())
     half = (x < nx // 2).astype(float)
     garbage = np.where(half > 0, lin, 50.0 + 7j)            # data outside M_T is ignored
-    assert np.allclose(oracle.smooth_map((ny, nx), 2, 0.7, half, ones, garbage), lin.ravel())
+    assert np.allclose(smooth_map((ny, nx), 2, 0.7, half, ones, garbage), lin.ravel())
     z = rng.normal(size=(ny, nx)) + 1j * rng.normal(size=(ny, nx))
-    assert np.allclose(oracle.smooth_map((ny, nx), 1, 0.0, ones, eps, z), z.ravel())
+    assert np.allclose(smooth_map((ny, nx), 1, 0.0, ones, eps, z), z.ravel())
+    # extrapolation along the other axes: trusted on half the rows (y), half the planes (z)
+    half_y = (y < ny // 2).astype(float)
+    garbage_y = np.where(half_y > 0, lin, -4.0 + 9j)
+    assert np.allclose(smooth_map((ny, nx), 2, 0.7, half_y, ones, garbage_y), lin.ravel())
     # 3D: a linear field along all three axes is kept by second differences
     zz, yy, xx = np.mgrid[:4, :5, :6]
     lin3 = 1.0 + 0.5 * xx - 0.25 * yy + 0.125j * zz
     o3 = np.ones((4, 5, 6))
-    assert np.allclose(oracle.smooth_map((4, 5, 6), 2, 2.0, o3, o3, lin3), lin3.ravel())
+    assert np.allclose(smooth_map((4, 5, 6), 2, 2.0, o3, o3, lin3), lin3.ravel())
+    half_z = (zz < 2).astype(float)
+    garbage_z = np.where(half_z > 0, lin3, 3.0)
+    assert np.allclose(smooth_map((4, 5, 6), 2, 2.0, half_z, o3, garbage_z), lin3.ravel())
 
 
 def test_smooth_map_weight_sits_on_the_row_voxel():
+    smooth_map_weight_pin(oracle.smooth_map)
+
+
+def smooth_map_weight_pin(smooth_map):
     """Three voxels, first differences (Eq. 3), alpha = 1, weights (1, 2, 5): the rows are
     w_0 (x1 - x0) and w_1 (x2 - x1) (the last voxel has no row, its weight is unused), so the
     normal matrix is I + [[1, -1, 0], [-1, 1 + 4, -4], [0, -4, 4]]."""
     N = np.eye(3) + np.array([[1.0, -1.0, 0.0], [-1.0, 5.0, -4.0], [0.0, -4.0, 4.0]])
     xhat = np.array([1.0, -2.0, 0.5j])
     expect = np.linalg.solve(N, xhat)
-    got = oracle.smooth_map((1, 3), 1, 1.0, np.ones(3), np.array([1.0, 2.0, 5.0]), xhat)
+    got = smooth_map((1, 3), 1, 1.0, np.ones(3), np.array([1.0, 2.0, 5.0]), xhat)
     assert np.allclose(got, expect)
+    # alpha scales the derivative part of the normal matrix linearly (alpha = 2 here)
+    got_a = smooth_map((1, 3), 1, 2.0, np.ones(3), np.array([1.0, 2.0, 5.0]), xhat)
+    assert np.allclose(got_a, np.linalg.solve(np.eye(3) + 2.0 * (N - np.eye(3)), xhat))
+    # a data weight w0 = (2, 1, 0.5) enters squared on both sides: diag(4, 1, 1/4) + the same
+    # derivative part, right-hand side (4, 1, 1/4) o xhat
+    N2 = np.diag([4.0, 1.0, 0.25]) + (N - np.eye(3))
+    expect2 = np.linalg.solve(N2, np.array([4.0, 1.0, 0.25]) * xhat)
+    got2 = smooth_map((1, 3), 1, 1.0, np.array([2.0, 1.0, 0.5]), np.array([1.0, 2.0, 5.0]), xhat)
+    assert np.allclose(got2, expect2)
+    # unconstrained voxels (w0 = 0, every touching row weighted 0) keep xhat; the others solve
+    # I + [[1, -1], [-1, 1]] on their own
+    xh4 = np.array([1.0 + 1.0j, -1.0, 7.0, -3.0j])
+    got4 = smooth_map((1, 4), 1, 1.0, np.array([1.0, 1.0, 0.0, 0.0]),
+                      np.array([1.0, 0.0, 0.0, 0.0]), xh4)
+    sub = np.linalg.solve(np.array([[2.0, -1.0], [-1.0, 2.0]]), xh4[:2])
+    assert np.allclose(got4, np.concatenate([sub, xh4[2:]]))
 
 
 def test_smooth_sensitivities_pins():
+    smooth_sensitivities_pins(oracle.smooth_sensitivities)
+
+
+def smooth_sensitivities_pins(smooth_sensitivities):
     """Per-coil smoothing of magnitude and normalised map (Eq. 1 as the paper applies it):
     a map with positive linear magnitude and constant phase, trusted on half the grid only, is
     returned exactly over the whole grid (both parts lie in the null space of the second
@@ -341,17 +384,34 @@ def test_smooth_sensitivities_pins():
     exact = np.stack([(1.0 + 0.2 * x + 0.1 * y) * np.exp(0.7j),
                       (2.0 + 0.05 * x - 0.1 * y) * np.exp(-2.1j)], axis=-1).reshape(-1, 2)
     garbage = np.where(half.ravel()[:, None] > 0, exact, 9.0 - 4.0j)
-    out = oracle.smooth_sensitivities((ny, nx), 0.8, half, ones, garbage)
+    out = smooth_sensitivities((ny, nx), 0.8, half, ones, garbage)
     assert np.allclose(out, exact)
     phase = np.exp(1j * 0.08 * (x - 4.5) ** 2).reshape(-1, 1)
     rng = np.random.default_rng(3)
     S = np.concatenate([phase, exact[:, :1], np.zeros((ny * nx, 1)),
                         rng.normal(size=(ny * nx, 1)) + 1j * rng.normal(size=(ny * nx, 1))],
                        axis=1)
-    out = oracle.smooth_sensitivities((ny, nx), 0.8, ones, ones, S)
+    out = smooth_sensitivities((ny, nx), 0.8, ones, ones, S)
     assert np.allclose(np.abs(out[:, 0]), 1.0)
     assert not np.allclose(out[:, 0], phase[:, 0], atol=1e-3)
     assert np.array_equal(out[:, 2], np.zeros(ny * nx))
     perm = [3, 0, 2, 1]
-    assert np.allclose(oracle.smooth_sensitivities((ny, nx), 0.8, ones, ones, S[:, perm]),
+    assert np.allclose(smooth_sensitivities((ny, nx), 0.8, ones, ones, S[:, perm]),
                        out[:, perm])
+    # very strong smoothing on a line of 5 voxels, all trusted: each field tends to its
+    # least-squares straight line, so S -> line(|S|) line(u) / |line(u)| with u = S / |S|
+    # (np.polyfit fits the lines); smoothing S itself would weight the phase by the magnitude
+    xs = np.arange(5.0)
+    S5 = ((np.array([1.0, 3.0, 0.5, 2.0, 4.0]) *
+           np.exp(1j * np.array([0.0, 1.2, -0.7, 2.0, 0.4])))).reshape(5, 1)
+    one5 = np.ones(5)
+    got5 = smooth_sensitivities((1, 5), 1e8, one5, one5, S5)[:, 0]
+
+    def line(v):
+        re = np.polyval(np.polyfit(xs, v.real, 1), xs)
+        im = np.polyval(np.polyfit(xs, v.imag, 1), xs) if np.iscomplexobj(v) else 0.0
+        return re + 1j * im
+
+    m_line = line(np.abs(S5[:, 0])).real
+    u_line = line(S5[:, 0] / np.abs(S5[:, 0]))
+    assert np.allclose(got5, m_line * u_line / np.abs(u_line), atol=1e-5)
