@@ -76,6 +76,15 @@ CASES = [
      [("axes=(1, 0)) / n", "axes=(1, 0))")]),
     ("uncentred frequency index", om.kspace_filter, pins.kspace_filter_pins,
      [("c = np.arange(n) - n // 2", "c = np.arange(n)")]),
+    # k-space mask
+    ("mask grid not centred", om.kspace_mask, pins.kspace_mask_pins,
+     [("u = 2 * np.pi * (np.arange(nx) - nx // 2) / (nx * dx)",
+       "u = 2 * np.pi * np.arange(nx) / (nx * dx)")]),
+    ("mask spacings swapped", om.kspace_mask, pins.kspace_mask_pins,
+     [("u = 2 * np.pi * (np.arange(nx) - nx // 2) / (nx * dx)",
+       "u = 2 * np.pi * (np.arange(nx) - nx // 2) / (nx * dy)")]),
+    ("mask axes swapped", om.kspace_mask, pins.kspace_mask_pins,
+     [("np.stack([U.ravel(), V.ravel()], axis=1)", "np.stack([V.ravel(), U.ravel()], axis=1)")]),
     # L-curve corner
     ("curvature sign reversed", om.lcurve_corner, pins.lcurve_pins,
      [("k = (dda * db - da * ddb) / den", "k = (da * ddb - dda * db) / den")]),
@@ -90,6 +99,7 @@ def test_the_real_oracle_passes_every_pin_used_here():
     pins.smooth_sensitivities_pins(om.smooth_sensitivities)
     pins.kspace_filter_pins(om.kspace_filter)
     pins.lcurve_pins(om.lcurve_corner)
+    pins.kspace_mask_pins(om.kspace_mask)
 
 
 @pytest.mark.parametrize("name,func,check,edits", CASES, ids=[c[0] for c in CASES])

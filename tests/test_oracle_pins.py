@@ -285,15 +285,29 @@ def kspace_filter_pins(kspace_filter):
 
 
 def test_kspace_mask_of_a_square_of_samples():
-    """Samples on the corners of a square cover exactly the Cartesian points inside it."""
+    kspace_mask_pins(oracle.kspace_mask)
+
+
+def kspace_mask_pins(kspace_mask):
+    """Samples on the corners of a rectangle cover exactly the Cartesian points inside it; the
+    grid spacing differs along x and y in the second case, and the grid is not square."""
     nx = ny = 8
     d = 0.01
     dk = 2 * np.pi / (nx * d)
     kx = np.array([-2.5, 2.5, 2.5, -2.5]) * dk
     ky = np.array([-1.5, -1.5, 1.5, 1.5]) * dk
-    m = oracle.kspace_mask(nx, ny, d, d, kx, ky)
+    m = kspace_mask(nx, ny, d, d, kx, ky)
     expect = np.zeros((ny, nx))
     expect[4 - 1: 4 + 2, 4 - 2: 4 + 3] = 1.0
+    assert np.array_equal(m, expect)
+    # 10 x 6 grid, dx = 0.01, dy = 0.02: k steps 2 pi / 0.1 along x and 2 pi / 0.12 along y
+    nx, ny, dx, dy = 10, 6, 0.01, 0.02
+    dkx, dky = 2 * np.pi / (nx * dx), 2 * np.pi / (ny * dy)
+    kx = np.array([-3.5, 1.5, 1.5, -3.5]) * dkx
+    ky = np.array([-0.5, -0.5, 2.5, 2.5]) * dky
+    m = kspace_mask(nx, ny, dx, dy, kx, ky)
+    expect = np.zeros((ny, nx))
+    expect[3 + 0: 3 + 3, 5 - 3: 5 + 2] = 1.0      # u - 5 in -3..1, v - 3 in 0..2
     assert np.array_equal(m, expect)
 
 
