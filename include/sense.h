@@ -153,10 +153,12 @@ int sense_cg_solve_iterates(sense_plan plan, const float* s, float* iterates,
                             const sense_cg_opts* opts, double* history, sense_cg_info* info,
                             void* stream);
 
-/* Maximum-curvature (L-curve corner) index over history rows 1..n-1 of a CG history
- * (format of sense_cg_solve): points (log ||E x_n - s||, log ||x_n||), curvature signed
- * positive for the clockwise turn at the corner, central differences; first maximum
- * wins. Host-only. *corner = -1 when n < 3. Errors: EINVAL. */
+/* Maximum-curvature (L-curve corner) iteration of a CG history of n rows (format of
+ * sense_cg_solve; "assessment of the number of CG iterations" in the paper's methods): the
+ * curve's points are (log ||E x_i - s||, log ||x_i||) for the iterates i = 1..n-1 (row 0, the
+ * start x_0 = 0, is not a point and is never read); curvature by central differences in i,
+ * signed positive for the clockwise turn at the corner; candidates i = 2..n-2, first maximum
+ * wins. Host-only. *corner = -1 when n < 4 (fewer than three points). Errors: EINVAL. */
 int sense_lcurve_corner(const double* history, int32_t n, int32_t* corner);
 
 /* Differentiation ----------------------------------------------------------------------

@@ -51,7 +51,7 @@ def load():
         lib.or_normal.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
                                   _ptr]
         lib.or_cg.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _int, _dbl,
-                              _int, _ptr, _ptr, _ptr]
+                              _int, _ptr, _ptr, _ptr, _ptr]
         lib.or_cg.restype = _int
         lib.or_grad_omega.argtypes = [_i64, _i64, _int, _int, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
                                       _ptr]
@@ -132,15 +132,21 @@ def normal(Kmat, Rmat, S, m, j=None):
 
 
 def cg(Kmat, Rmat, S, sigma, n_it, j=None, rel_tol=0.0, apply_j=True, history=False,
-       iterates=False):
-    """The CG loop of Alg. 1 (Fig. 2). Returns dict(x, iters, history?, iterates?)."""
+       iterates=False, x0=None):
+    """The CG loop of Alg. 1 (Fig. 2). Returns dict(x, iters, history?, iterates?).
+
+    x0: optional start rho_0 ([L], the iterate before the final multiplication by j);
+    Alg. 1 starts from rho_0 = 0. rel_tol stops once ||r_n|| <= rel_tol ||E^H sigma||."""
     Kmat, Rmat, S, jj, L, K, C, P1 = _geom(Kmat, Rmat, S, j)
     sigma = _c(sigma, np.complex128).reshape(K, C)
     rho = np.empty(L, np.complex128)
     hist = np.full((n_it + 1, 3), np.nan) if history else None
     its = np.zeros((n_it + 1, L), np.complex128) if iterates else None
+    xs = None if x0 is None else _c(x0, np.complex128)
+    if xs is not None and xs.shape != (L,):
+        raise ValueError("x0 must be [L]")
     n = load().or_cg(L, K, C, P1, _p(Kmat), _p(Rmat), _p(S), _p(jj), _p(sigma), int(n_it),
-                     float(rel_tol), 1 if apply_j else 0, _p(rho), _p(hist), _p(its))
+                     float(rel_tol), 1 if apply_j else 0, _p(xs), _p(rho), _p(hist), _p(its))
     out = {"x": rho, "iters": int(n)}
     if history:
         out["history"] = hist[: n + 1]
@@ -272,18 +278,20 @@ def kspace_filter(image, shape, mask):
 
 
 def lcurve_corner(res_norm, sol_norm):
-    """Index n (into the given arrays) of maximum L-curve curvature.
+    """Iteration n of maximum L-curve curvature.
 
-    The L-curve is the parametric curve (a, b) = (log ||E x_n - s||, log ||x_n||) over the
-    CG iterations n; the proposed stop is its point of maximum curvature. CG first moves
-    along the flat leg (the residual falls) and then up the steep leg (the solution norm
-    grows), so the corner is a clockwise turn; the curvature is signed positive for
-    clockwise turns: kappa = (a'' b' - a' b'') / (a'^2 + b'^2)^1.5, derivatives by central
-    differences in n. Only interior points are candidates and the first maximum wins.
-    Returns -1 when fewer than three points are given.
+    res_norm[n], sol_norm[n] are ||E x_n - s|| and ||x_n|| for n = 0..N (the rows of a CG
+    history). The L-curve is the parametric curve (a, b) = (log ||E x_n - s||, log ||x_n||)
+    over the iterates n = 1..N; row 0 (the start x_0 = 0, whose log norm is -inf) is not a
+    point of it and is never read. The proposed stop is the point of maximum curvature. CG
+    first moves along the flat leg (the residual falls) and then up the steep leg (the
+    solution norm grows), so the corner is a clockwise turn; the curvature is signed positive
+    for clockwise turns: kappa = (a'' b' - a' b'') / (a'^2 + b'^2)^1.5, derivatives by central
+    differences in n. Only interior points (n = 2..N-1) are candidates and the first maximum
+    wins. Returns -1 when the curve has fewer than three points (N < 3).
     """
-    a = np.log(np.asarray(res_norm, np.float64))
-    b = np.log(np.asarray(sol_norm, np.float64))
+    a = np.log(np.asarray(res_norm, np.float64)[1:])
+    b = np.log(np.asarray(sol_norm, np.float64)[1:])
     n = a.shape[0]
     if n < 3:
         return -1
@@ -298,5 +306,5 @@ def lcurve_corner(res_norm, sol_norm):
             continue
         k = (dda * db - da * ddb) / den
         if k > best_k:
-            best, best_k = i, k
+            best, best_k = i + 1, k      # point i of the curve is iteration i + 1
     return best

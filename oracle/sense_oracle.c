@@ -127,7 +127,10 @@ static double norm2(const cplx* a, int64_t n) { return sqrt(creal(dotc(a, a, n))
 /* The CG loop of Alg. 1 (Fig. 2): CG on E^H E rho = E^H sigma from rho = 0.
  *
  *  n_it      N_It, the number of iterations (fixed-count stop, the paper's choice)
- *  rel_tol   extra stop when ||r_n|| <= rel_tol ||r_0|| (0 disables; not in the paper)
+ *  rel_tol   extra stop when ||r_n|| <= rel_tol ||E^H sigma|| (0 disables; not in the paper;
+ *            from rho_0 = 0 the threshold is rel_tol ||r_0||)
+ *  x0        optional [L] start rho_0 (NULL: rho_0 = 0 as in Alg. 1); the first residual
+ *            is then r_0 = E^H sigma - E^H E rho_0 and the first direction p_0 = r_0
  *  rho       output [L]; multiplied by j at the end (as Alg. 1 does) when apply_j != 0
  *  hist      optional [(n_it+1)][3]: ||r_n||, ||rho_n||, ||E rho_n - sigma|| for
  *            n = 0..iters (row 0 is the start, rho_0 = 0); unused rows are left as is
@@ -136,18 +139,24 @@ static double norm2(const cplx* a, int64_t n) { return sqrt(creal(dotc(a, a, n))
  * Alg. 1 keeps them (alpha = r^H r, beta = p^H q, rho += alpha/beta p ...).      */
 int or_cg(int64_t L, int64_t K, int C, int P1, const double* Km, const double* Rm,
           const cplx* S, const double* j, const cplx* sigma, int n_it, double rel_tol,
-          int apply_j, cplx* rho, double* hist, cplx* iterates) {
+          int apply_j, const cplx* x0, cplx* rho, double* hist, cplx* iterates) {
   cplx* p = (cplx*)malloc(sizeof(cplx) * (size_t)L);
   cplx* r = (cplx*)malloc(sizeof(cplx) * (size_t)L);
   cplx* q = (cplx*)malloc(sizeof(cplx) * (size_t)L);
   cplx* work = (cplx*)malloc(sizeof(cplx) * (size_t)(K * C));
   cplx* resid = hist ? (cplx*)malloc(sizeof(cplx) * (size_t)(K * C)) : NULL;
 
-  /* start: p = E^H sigma, r = p, rho = 0 */
-  or_adjoint(L, K, C, P1, Km, Rm, S, j, sigma, NULL, L, p);
-  memcpy(r, p, sizeof(cplx) * (size_t)L);
-  for (int64_t l = 0; l < L; ++l) rho[l] = 0.0;
-  const double r0 = norm2(r, L);
+  /* start: r = E^H sigma (- E^H E rho_0), p = r, rho = rho_0 (0 in Alg. 1) */
+  or_adjoint(L, K, C, P1, Km, Rm, S, j, sigma, NULL, L, r);
+  const double r0 = norm2(r, L);   /* ||E^H sigma||: the tolerance reference */
+  if (x0) {
+    memcpy(rho, x0, sizeof(cplx) * (size_t)L);
+    or_normal(L, K, C, P1, Km, Rm, S, j, rho, q, work);
+    for (int64_t l = 0; l < L; ++l) r[l] -= q[l];
+  } else {
+    for (int64_t l = 0; l < L; ++l) rho[l] = 0.0;
+  }
+  memcpy(p, r, sizeof(cplx) * (size_t)L);
 
   int done = 0;
   for (int n = 0;; ++n) {

@@ -488,9 +488,11 @@ extern "C" const char* sense_last_error(void) { return g_last_error.c_str(); }
 extern "C" int sense_lcurve_corner(const double* h, int32_t n, int32_t* corner) {
   if (!h || !corner || n < 0) return set_error(SENSE_EINVAL, "null history/corner or n < 0");
   *corner = -1;
-  if (n < 3) return SENSE_OK;
+  // the curve's points are the iterates, rows 1..n-1 (row 0 is the start x_0 = 0, whose
+  // log norm is -inf, and is never read); interior points 2..n-2 are the candidates
+  if (n < 4) return SENSE_OK;
   double best = -INFINITY;
-  for (int i = 1; i < n - 1; ++i) {
+  for (int i = 2; i < n - 1; ++i) {
     // a = log data residual (column 2), b = log solution norm (column 1)
     const double am = std::log(h[3 * (i - 1) + 2]), a0 = std::log(h[3 * i + 2]),
                  ap = std::log(h[3 * (i + 1) + 2]);

@@ -91,6 +91,12 @@ CASES = [
     ("minimum instead of maximum", om.lcurve_corner, pins.lcurve_pins,
      [("best, best_k = -1, -np.inf", "best, best_k = -1, np.inf"),
       ("if k > best_k:", "if k < best_k:")]),
+    ("the start x_0 read as a point of the curve", om.lcurve_corner, pins.lcurve_pins,
+     [("a = np.log(np.asarray(res_norm, np.float64)[1:])",
+       "a = np.log(np.asarray(res_norm, np.float64))"),
+      ("b = np.log(np.asarray(sol_norm, np.float64)[1:])",
+       "b = np.log(np.asarray(sol_norm, np.float64))"),
+      ("best, best_k = i + 1, k", "best, best_k = i, k")]),
 ]
 
 
@@ -122,6 +128,8 @@ OPERATOR_PINS = ["test_closed_form_dft_matches_numpy_fft", "test_point_source_an
 CG_PINS = ["test_cg_converges_to_dense_normal_solution",
            "test_cg_iterates_minimise_error_over_krylov_space",
            "test_cg_history_and_residual_monotone"]
+X0_PINS = ["test_cg_from_x0_minimises_error_over_shifted_krylov_space",
+           "test_cg_from_the_solution_stops_at_once"]
 GRAD_PINS = ["test_grad_omega_matches_central_differences",
              "test_grad_omega_adjoint_matches_central_differences"]
 
@@ -146,6 +154,16 @@ C_CASES = [
      [("acc += conj(a[i]) * b[i];", "acc += a[i] * b[i];")]),
     ("CG ends dividing by j", CG_PINS,
      [("rho[l] *= j[l];", "rho[l] /= j[l];")]),
+    ("CG from x0 keeps r_0 = E^H s", X0_PINS,
+     [("for (int64_t l = 0; l < L; ++l) r[l] -= q[l];", "")]),
+    ("CG from x0 starts at zero", X0_PINS,
+     [("memcpy(rho, x0, sizeof(cplx) * (size_t)L);",
+       "for (int64_t l = 0; l < L; ++l) rho[l] = 0.0;")]),
+    ("CG tolerance relative to the start residual", X0_PINS,
+     [("const double r0 = norm2(r, L);   /* ||E^H sigma||: the tolerance reference */",
+       "double r0;"),
+      ("  memcpy(p, r, sizeof(cplx) * (size_t)L);\n",
+       "  memcpy(p, r, sizeof(cplx) * (size_t)L);\n  r0 = norm2(r, L);\n")]),
     ("B0 gradient with the wrong time factor sign", GRAD_PINS,
      [("(-I * Km[kappa * P1 + 0])", "(I * Km[kappa * P1 + 0])")]),
     ("adjoint B0 gradient with the wrong time factor sign", GRAD_PINS,
@@ -173,7 +191,7 @@ def _run_pin(name, fixtures):
 
 
 def test_the_real_c_oracle_passes_the_pins_used_here(pin_fixtures):
-    for name in OPERATOR_PINS + CG_PINS + GRAD_PINS:
+    for name in OPERATOR_PINS + CG_PINS + X0_PINS + GRAD_PINS:
         _run_pin(name, pin_fixtures)
 
 

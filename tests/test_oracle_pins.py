@@ -163,6 +163,53 @@ def test_cg_iterates_minimise_error_over_krylov_space(tiny):
         krylov.append(A @ krylov[-1] / np.linalg.norm(A @ krylov[-1]))
 
 
+def test_cg_from_x0_minimises_error_over_shifted_krylov_space(tiny):
+    """From a start x_0: x_n = x_0 + argmin over K_n(A, r_0) of ||x - x*||_A with
+    r_0 = b - A x_0, and history row 0 holds ||r_0||, ||x_0||, ||E x_0 - s||."""
+    wl, sigma, E = tiny
+    A = E.conj().T @ E
+    b = E.conj().T @ sigma.ravel()
+    rng = np.random.default_rng(17)
+    x0 = wl.m_true + 0.3 * _crandn(rng, wl.L)
+    r0 = b - A @ x0
+    n_it = 5
+    out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, n_it, j=wl.j, apply_j=False, iterates=True,
+                    history=True, x0=x0)
+    its, h = out["iterates"], out["history"]
+    assert _rel(its[0], x0) == 0.0
+    assert abs(h[0, 0] - np.linalg.norm(r0)) < 1e-10 * np.linalg.norm(b)
+    assert abs(h[0, 1] - np.linalg.norm(x0)) < 1e-12 * np.linalg.norm(x0)
+    assert abs(h[0, 2] - np.linalg.norm(E @ x0 - sigma.ravel())) < 1e-10 * np.linalg.norm(sigma)
+    krylov = [r0 / np.linalg.norm(r0)]
+    for n in range(1, n_it + 1):
+        V, _ = np.linalg.qr(np.stack(krylov, axis=1))
+        xn = x0 + V @ np.linalg.solve(V.conj().T @ A @ V, V.conj().T @ r0)
+        assert _rel(its[n], xn) < 1e-8, n
+        krylov.append(A @ krylov[-1] / np.linalg.norm(A @ krylov[-1]))
+
+
+def test_cg_from_the_solution_stops_at_once(tiny):
+    """Started at the dense solution x* the residual is already at rounding level: the
+    tolerance stop (relative to ||E^H s||) ends the solve after 0 iterations at x*."""
+    wl, sigma, E = tiny
+    A = E.conj().T @ E
+    b = E.conj().T @ sigma.ravel()
+    x_star = np.linalg.solve(A, b)
+    out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 10, j=wl.j, apply_j=False, rel_tol=1e-9,
+                    x0=x_star, history=True)
+    assert out["iters"] == 0
+    assert _rel(out["x"], x_star) == 0.0
+    assert out["history"][0, 0] < 1e-9 * np.linalg.norm(b)
+    # a start near x* reaches the same tolerance in fewer iterations than x_0 = 0
+    tol = 1e-4
+    cold = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 60, j=wl.j, apply_j=False, rel_tol=tol)
+    rng = np.random.default_rng(3)
+    warm = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 60, j=wl.j, apply_j=False, rel_tol=tol,
+                     x0=x_star + 1e-3 * np.linalg.norm(x_star) / np.sqrt(wl.L) * _crandn(rng, wl.L))
+    assert 0 < warm["iters"] < cold["iters"]
+    assert _rel(warm["x"], x_star) < 1e-3
+
+
 def test_cg_history_and_residual_monotone(tiny):
     wl, sigma, E = tiny
     out = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma, 12, j=wl.j, apply_j=False, history=True,
@@ -240,14 +287,30 @@ def test_grad_omega_adjoint_matches_central_differences(small):
 
 
 def lcurve_pins(lcurve_corner):
-    """(a, b) = (x, x^2) traversed right to left: curvature peaks (value 2) at the vertex."""
+    """(a, b) = (x, x^2) traversed right to left: curvature peaks (value 2) at the vertex.
+    The arrays are CG-history columns: entry n belongs to iterate n, and entry 0 (the start
+    x_0 = 0) is not a point of the L-curve (the curve runs over n = 1..N)."""
     xs = np.linspace(2.0, -1.0, 31)           # vertex at index 20
     idx = lcurve_corner(np.exp(xs), np.exp(xs ** 2))
     assert idx == 20
     # a shifted vertex moves the corner with it
     xs2 = xs + 0.5                             # vertex now where xs == -0.5 -> index 25
     assert lcurve_corner(np.exp(xs2), np.exp((xs2 - 0.0) ** 2)) == 25
+    # fewer than three iterates (entries 1..N, N < 3): no corner
     assert lcurve_corner([1.0, 2.0], [1.0, 1.0]) == -1
+    assert lcurve_corner([1.0, 2.0, 3.0], [0.0, 1.0, 2.0]) == -1
+    # a real history starts with ||x_0|| = 0: entry 0 is never read (no log of zero)
+    sol = np.exp(xs ** 2)
+    sol[0] = 0.0
+    with np.errstate(all="raise"):
+        assert lcurve_corner(np.exp(xs), sol) == 20
+    # vertex at iteration 2, the first interior point of the curve; an entry 0 that would make
+    # iteration 1 the sharpest turn if it were a point does not move the corner
+    h = 0.1
+    x = np.array([3 * h] + [(2 - n) * h for n in range(1, 31)])
+    res, sol = np.exp(x), np.exp(x ** 2)
+    sol[0] = np.exp(3 * h)
+    assert lcurve_corner(res, sol) == 2
 
 
 def test_lcurve_corner_on_parabola_vertex():
