@@ -112,7 +112,7 @@ int sense_adjoint(sense_plan plan, int prec, const float* s, float* m, void* str
 int sense_normal_op(sense_plan plan, int prec, const float* m, float* out, void* stream);
 
 /* CG options. Stopping: the paper's fixed iteration count N_It (max_iter), optionally
- * also ||r_n|| <= rel_tol ||r_0|| (r_0 = E^H s). */
+ * also ||r_n|| <= rel_tol ||E^H s|| (the residual of rho = 0). */
 typedef struct {
   int32_t max_iter;     /* N_It >= 0                                                   */
   int32_t prec;         /* sense_precision of E^H E inside the iterations              */
@@ -121,6 +121,9 @@ typedef struct {
                            b - E^H E x with the FP32 operator every this many
                            iterations (0 = never)                                      */
   int32_t apply_j;      /* nonzero: multiply the result by j (as Alg. 1 ends)          */
+  int32_t use_x0;       /* nonzero: x holds the start rho_0 on input (sense_cg_solve and
+                           sense_cg_solve_iterates; a solve resumed from an earlier result
+                           passes that result computed with apply_j = 0)               */
 } sense_cg_opts;
 
 typedef struct {
@@ -130,9 +133,13 @@ typedef struct {
   double rr_final;      /* r_n^H r_n at exit                                           */
 } sense_cg_info;
 
-/* rho = CG(E^H E, E^H s) (the CG loop of Alg. 1, Fig. 2), starting from rho = 0.
+/* rho = CG(E^H E, E^H s) (the CG loop of Alg. 1, Fig. 2), starting from rho = 0 or, with
+ * opts->use_x0, from the rho_0 given in x (then r_0 = E^H s - E^H E rho_0 and p_0 = r_0, with
+ * E^H E in the iteration precision, or FP32 when refine_every > 0). A zero residual at the
+ * start (E^H s = 0, or a start that solves the system exactly) ends the solve after 0
+ * iterations with SENSE_OK.
  *   s        [K][C] complex64 coil data Sigma (device or host)
- *   x        [L] complex64 output rho (device or host)
+ *   x        [L] complex64 output rho (device or host); input rho_0 too with use_x0
  *   history  NULL or HOST double[(max_iter+1)*3]: for n = 0..iters the row
  *            (||r_n||, ||rho_n||, ||E rho_n - s||) -- the L-curve coordinates; the data
  *            residual uses ||E x - s||^2 = ||s||^2 - Re<x,b> - Re<x,r> (r = b - E^H E x)
@@ -145,7 +152,8 @@ int sense_cg_solve(sense_plan plan, const float* s, float* x, const sense_cg_opt
 
 /* sense_cg_solve that also records every iterate: iterates is DEVICE memory of
  * (max_iter + 1) x L complex64, row n = rho_n in user voxel order (multiplied by j when
- * apply_j, like the result); row 0 is zero and rows after a tolerance stop repeat the final
+ * apply_j, like the result); row 0 is zero (with use_x0: the start rho_0, read from row 0 on
+ * input and rewritten times j when apply_j) and rows after a tolerance stop repeat the final
  * iterate; the result itself is row max_iter. Used to study stopping rules against a known
  * image (the paper compares the L-curve corner with SSIM over the iterations). Errors as
  * sense_cg_solve, plus EINVAL for host memory. */
@@ -205,16 +213,21 @@ int sense_cg_backward(sense_plan plan, const float* s, const void* ckpt, int64_t
  * whose device memory is owned by another framework's allocator, can neither create a plan
  * nor let a call allocate. This entry point takes the problem directly and allocates
  * nothing: its only scratch (the partial sums of the voxel-split FP32 encode) is a fixed
- * 16 MiB array inside the library, which every GPU that loads the library holds until the
- * process exits. Phases are evaluated per pair in FP64 (no plan, no anchors), the rest as
- * in the FP32 path.
+ * 16 MiB array inside the library. Phases are evaluated per pair in FP64 (no plan, no
+ * anchors), the rest as in the FP32 path.
  *   Kmat [K][P1] float64, Rmat [P1][L] float64, S [L][C] complex64, j [L] float32 or NULL,
  *   m [L] complex64: DEVICE inputs; s [K][C] complex64: DEVICE output (caller-owned).
  * Limits: C <= 64, P1 <= 24, K x (C rounded up to 8/16/32/64) <= 2^21; larger sizes are
- * rejected with SENSE_EINVAL and a message. The first call on a device looks up the
- * array's device address (with that device current); make that first call before any
- * stream capture. All calls share the array, which keeps the last call's partial sums;
- * calls that overlap on the GPU (other streams, other host threads) race on it.
+ * rejected with SENSE_EINVAL and a message.
+ * First call on a device: CUDA loads the library's device code lazily, so the 16 MiB array
+ * comes into existence on a device only when this entry point first runs there, and that
+ * first call also looks up the array's device address (with that device current) and caches
+ * it for the life of the process. A caller that reserves the GPU's memory up front should
+ * therefore make one call (any valid size) before reserving, and before any stream capture;
+ * from then on the array stays resident on that device until the process exits. The cached
+ * address does not survive cudaDeviceReset(): do not call this entry point on a device after
+ * resetting it. All calls share the array, which keeps the last call's partial sums; calls
+ * that overlap on the GPU (other streams, other host threads) race on it.
  * Asynchronous on `stream`. Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 int sense_encode_noalloc(int64_t L, int64_t K, int32_t C, int32_t P1, const double* Kmat,
                          const double* Rmat, const float* S, const float* j, const float* m,
@@ -345,12 +358,22 @@ int sense_plan_store_p(sense_plan plan, int32_t enable, void* stream);
  * (no counterpart in the paper: execution parameters of the tensor-core kernels)
  *   seg_len  the tensor-core passes accumulate at most this many 128 x 128 (sample, voxel)
  *            blocks in one FP32 tensor-memory accumulator before adding it to a running
- *            sum; shorter = more accurate, longer = fewer drains. 1..64, default 8.
- *   grid     persistent CTAs of a tensor-core pass; 0 = one per SM (default). */
+ *            sum; shorter = more accurate, longer = fewer drains. 1..64, default 4.
+ *   grid     persistent CTAs of a tensor-core pass; 0 = one per SM (default).
+ *   wait_limit_us  every wait inside a tensor-core pass gives up after this long (measured
+ *            in SM clock cycles at the maximum clock); the CTA then records the failure,
+ *            completes what it issued, frees its tensor memory and returns, and the next
+ *            synchronising call (or sense_plan_sync) reports SENSE_ETIMEOUT. 0 = about 2 s
+ *            (default); at most 6e7.
+ *   test_hold_stage  for tests of that time-out path only: when > 0, the loader warp of CTA 0
+ *            never signals the arrival of its stage number test_hold_stage (counted from 1),
+ *            so the waits on it run out; 0 = off (default). */
 typedef struct {
   int32_t seg_len;
   int32_t grid;
-  int32_t reserved[6];
+  int32_t wait_limit_us;
+  int32_t test_hold_stage;
+  int32_t reserved[4];
 } sense_tuning;
 
 int sense_plan_get_tuning(sense_plan plan, sense_tuning* out);

@@ -364,6 +364,8 @@ extern "C" int sense_batch_cg_solve(sense_batch B, const float* const* s, float*
     return set_error(SENSE_EINVAL, "max_iter and rel_tol must be >= 0");
   if (opts->refine_every != 0)
     return set_error(SENSE_EINVAL, "batched solves do not support residual replacement");
+  if (opts->use_x0)
+    return set_error(SENSE_EINVAL, "batched solves start from rho = 0 (use_x0 must be 0)");
   if (opts->prec != SENSE_PREC_TC_FP16 && opts->prec != SENSE_PREC_TC_SPLIT)
     return set_error(SENSE_EINVAL, "batched solves run on the tensor cores (TC_FP16, TC_SPLIT)");
   const int n = (int)B->plans.size();

@@ -116,11 +116,55 @@ __global__ void __launch_bounds__(VB) cg_init_kernel(const float2* __restrict__ 
     scal[SC_ITER] = 0.0;
     scal[SC_TOL2] = rel_tol > 0.0 ? rel_tol * rel_tol * tot[0] : 0.0;
     scal[SC_MAXIT] = (double)max_iter;
-    scal[SC_STOP] = (max_iter <= 0) ? 1.0 : (isfinite(tot[0]) ? 0.0 : 3.0);
+    // a zero residual (no data, or b = 0) is already the solution: stop as converged
+    scal[SC_STOP] = (max_iter <= 0 || tot[0] == 0.0) ? 1.0 : (isfinite(tot[0]) ? 0.0 : 3.0);
     if (hist) {
       hist[0] = sqrt(tot[0]);
       hist[1] = 0.0;
       hist[2] = sqrt(scal[SC_SS]);
+    }
+  }
+}
+
+// start from rho_0 = x (plan order, already in place): with q = E^H E x, r = p = b - q;
+// rr0 = r^H r, the tolerance relative to ||b||; history row 0 of the start
+__global__ void __launch_bounds__(VB) cg_init_x0_kernel(const float2* __restrict__ b,
+                                                        const float2* __restrict__ q,
+                                                        const float2* __restrict__ x, float2* r,
+                                                        float2* p, int64_t Lp, double* part,
+                                                        unsigned* counter, double* scal,
+                                                        double* hist, double rel_tol,
+                                                        int max_iter) {
+  __shared__ double sh[5 * VB / 32];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Lp;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 bi = b[i], qi = q[i], xi = x[i];
+    const float2 ri = make_float2(bi.x - qi.x, bi.y - qi.y);
+    r[i] = ri;
+    p[i] = ri;
+    v[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    v[1] += (double)bi.x * bi.x + (double)bi.y * bi.y;
+    v[2] += (double)xi.x * bi.x + (double)xi.y * bi.y;   // Re <x, b>
+    v[3] += (double)xi.x * ri.x + (double)xi.y * ri.y;   // Re <x, r>
+    v[4] += (double)xi.x * xi.x + (double)xi.y * xi.y;
+  }
+  block_sum<5>(v, sh);
+  double tot[5];
+  if (finish_sums<5>(v, part, counter, tot)) {
+    scal[SC_RR] = tot[0];
+    scal[SC_RR0] = tot[0];
+    scal[SC_ITER] = 0.0;
+    scal[SC_TOL2] = rel_tol > 0.0 ? rel_tol * rel_tol * tot[1] : 0.0;
+    scal[SC_MAXIT] = (double)max_iter;
+    const bool fin = isfinite(tot[0]) && isfinite(tot[4]);
+    const bool done = max_iter <= 0 || tot[0] == 0.0 ||
+                      (scal[SC_TOL2] > 0.0 && tot[0] <= scal[SC_TOL2]);
+    scal[SC_STOP] = !fin ? 3.0 : (done ? 1.0 : 0.0);
+    if (hist) {
+      hist[0] = sqrt(tot[0]);
+      hist[1] = sqrt(tot[4]);
+      hist[2] = sqrt(fmax(0.0, scal[SC_SS] - tot[2] - tot[3]));
     }
   }
 }
@@ -475,7 +519,7 @@ extern "C" int sense_cg_solve_iterates(sense_plan P, const float* s, float* iter
   TRY(check_prec(opts->prec));
   if (!is_device_pointer(iterates)) return set_error(SENSE_EINVAL, "iterates must be device memory");
   float2* X = (float2*)iterates;
-  // the final iterate is row max_iter
+  // the start rho_0 (use_x0) is read from row 0; the final iterate is row max_iter
   return cg_run(P, s, (float*)(X + (size_t)opts->max_iter * P->L), opts, history, info, 0,
                 nullptr, X, (cudaStream_t)stream);
 }
@@ -493,9 +537,10 @@ extern "C" int sense_cg_solve(sense_plan P, const float* s, float* x, const sens
 namespace sense {
 
 // Steps 1-5 for data s (device, user layout): coil data in the internal layout, ||s||^2,
-// b = E^H s, x = 0, r = p = b, r^H r and the stopping thresholds.
+// b = E^H s, x = 0 (or x = x0, device, user order, when x0 is given), r = p = b - E^H E x,
+// r^H r and the stopping thresholds.
 int cg_begin(sense_plan_s* P, const float2* s, const sense_cg_opts* opts, double* hist,
-             cudaStream_t st) {
+             cudaStream_t st, const float2* x0) {
   const int vb = grid_for(P, P->Lp);
   const int yb = grid_for(P, P->Kp * P->Cp);
   TRY(load_data(P, s, P->Ydata, st));
@@ -509,8 +554,17 @@ int cg_begin(sense_plan_s* P, const float2* s, const sense_cg_opts* opts, double
                          ? SENSE_PREC_TC_SPLIT
                          : SENSE_PREC_FP32;
   TRY(adjoint_internal(P, prec_b, P->Ydata, P->vb, nullptr, st));
-  cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
-                                    P->scal, hist, opts->rel_tol, opts->max_iter);
+  if (x0) {
+    // r_0 = b - E^H E rho_0 with the operator b was made with
+    TRY(gather_image(P, x0, P->vx, st));
+    TRY(apply_normal_internal(P, prec_b, P->vx, P->vq, nullptr, st));
+    cg_init_x0_kernel<<<vb, VB, 0, st>>>(P->vb, P->vq, P->vx, P->vr, P->vp, P->Lp, P->red,
+                                         P->counter, P->scal, hist, opts->rel_tol,
+                                         opts->max_iter);
+  } else {
+    cg_init_kernel<<<vb, VB, 0, st>>>(P->vb, P->vr, P->vp, P->vx, P->Lp, P->red, P->counter,
+                                      P->scal, hist, opts->rel_tol, opts->max_iter);
+  }
   SENSE_CUDA_TRY(cudaGetLastError());
   count_launch(P);
   return SENSE_OK;
@@ -549,11 +603,24 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
   }
   Staged in;
   TRY(stage_in(s, P->stage_s, (size_t)P->K * P->C * 8, st, &in));
+  // the start rho_0 (use_x0): from x, or from row 0 of the iterates; staged through the same
+  // buffer as the result, which is written only after the start has been read
+  const float2* x0 = nullptr;
+  if (opts->use_x0) {
+    if (iterates) {
+      x0 = iterates;
+    } else {
+      Staged xin;
+      TRY(stage_in(x, P->stage_m, (size_t)P->L * 8, st, &xin));
+      x0 = (const float2*)xin.dev;
+    }
+  }
   Staged out = stage_out(x, P->stage_m);
   const int vb = grid_for(P, P->Lp);
-  TRY(cg_begin(P, (const float2*)in.dev, opts, P->hist, st));
+  TRY(cg_begin(P, (const float2*)in.dev, opts, P->hist, st, x0));
   const double* stop = P->scal + SC_STOP;
-  if (iterates) SENSE_CUDA_TRY(cudaMemsetAsync(iterates, 0, (size_t)P->L * 8, st));
+  if (iterates && !x0) SENSE_CUDA_TRY(cudaMemsetAsync(iterates, 0, (size_t)P->L * 8, st));
+  if (iterates && x0 && opts->apply_j) TRY(scatter_image(P, P->vx, iterates, true, st));
   for (int n = 0; n < N; ++n) {
     if (ckpt_every > 0 && n % ckpt_every == 0) TRY(ckpt_save(P, ckpt, n / ckpt_every, st));
     // q = E^H E p

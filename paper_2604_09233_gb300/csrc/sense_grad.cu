@@ -413,6 +413,8 @@ extern "C" int sense_cg_solve_ckpt(sense_plan P, const float* s, float* x,
     return set_error(SENSE_EINVAL, "max_iter, rel_tol must be >= 0 and ckpt_every >= 1");
   if (opts->refine_every != 0)
     return set_error(SENSE_EINVAL, "checkpointed solves do not support residual replacement");
+  if (opts->use_x0)
+    return set_error(SENSE_EINVAL, "checkpointed solves start from rho = 0 (use_x0 must be 0)");
   GTRY(check_prec(opts->prec));
   if (!is_device_pointer(ckpt) || ((uintptr_t)ckpt & 15))
     return set_error(SENSE_EINVAL, "ckpt must be 16-byte aligned device memory");

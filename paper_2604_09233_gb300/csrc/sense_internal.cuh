@@ -107,6 +107,10 @@ struct sense_plan_s {
   int tc_grid = 0;                 // persistent CTAs launched (<= pairs of blocks)
   int tc_grid_req = 0;             // requested CTAs (one per SM by default)
   int tc_seg_len = 4;              // drain the TMEM accumulators every this many pairs
+  int tc_wait_us = 0;              // bounded-wait limit of the tensor-core kernels (0: ~2 s)
+  long long tc_wait_cycles = 0;    // the same in SM clock cycles (0: the kernel's default)
+  int tc_test_hold = 0;            // time-out tests: stage CTA 0's loader withholds (+1)
+  int clock_khz = 0;               // maximum SM clock (cudaDevAttrClockRate)
   int min_rt = 0;                  // lower bound on RT (uniform kernels across a batch)
   int64_t geom_version = 0;        // incremented whenever the geometry arrays are rebuilt
   int tc_slots_e = 1, tc_slots_a = 1;
@@ -217,7 +221,7 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
            double* history, sense_cg_info* info, int ckpt_every, uint8_t* ckpt,
            float2* iterates, cudaStream_t st);
 int cg_begin(sense_plan_s* P, const float2* s_dev, const sense_cg_opts* opts, double* hist,
-             cudaStream_t st);
+             cudaStream_t st, const float2* x0 = nullptr);
 int cg_read_info(sense_plan_s* P, sense_cg_info* info, int* iters, cudaStream_t st);
 int encode_internal(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int,
                     cudaStream_t st);

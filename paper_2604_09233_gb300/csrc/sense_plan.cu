@@ -390,6 +390,14 @@ int plan_create(const sense_problem* prob, int min_cp, int min_rt, sense_plan_s*
   sense_plan_s* P = new sense_plan_s();
   P->device = dev;
   P->num_sms = prop.multiProcessorCount;
+  {
+    int khz = 0;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+      cudaGetLastError();
+      khz = 0;
+    }
+    P->clock_khz = khz > 0 ? khz : 2100000;
+  }
   P->L = L; P->K = K; P->C = C; P->P1 = P1;
   P->Lp = (L + TILE - 1) / TILE * TILE;
   P->Kp = (K + TILE - 1) / TILE * TILE;

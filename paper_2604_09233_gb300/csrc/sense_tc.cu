@@ -42,7 +42,7 @@ constexpr int MMA_WARP = 16;
 constexpr int LOAD_WARP = 17;
 constexpr int NTHREADS = 18 * 32;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000ll;  // ~2 s, when Params::wait_limit is 0
 
 // ---------------------------------------------------------------------------------------
 // PTX wrappers
@@ -77,16 +77,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait. Returns false (and raises the CTA abort flag and the global error word)
-// after WAIT_LIMIT_CYCLES, or immediately once another thread has aborted.
+// after `limit` SM clock cycles, or immediately once another thread has aborted.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                       int* err, int site) {
+                                       int* err, int site, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63u) == 0u) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+      if (clock64() - t0 > limit) {
         *abort_flag = 1;
         atomicCAS(err, 0, site);
         return false;
@@ -98,9 +98,9 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
 // Warp-uniform bounded wait: lane 0 polls, every lane gets the outcome and the warp is
 // converged on return (required before .sync.aligned tcgen05 instructions).
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int site) {
+                                          int* err, int site, long long limit) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err, site) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err, site, limit) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   return ok != 0;
@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
 
   const long long i = blockIdx.x;
   const int F = p.seg_len;
+  const long long LIM = p.wait_limit > 0 ? p.wait_limit : WAIT_LIMIT_CYCLES;
 
   if (threadIdx.x == 0) {
     for (int b = 0; b < NBUF; ++b) {
@@ -352,7 +353,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       auto push = [&](int b, int o, int in, int flags, int slot) -> bool {
         const int buf = (int)(it % NBUF);
         const uint32_t use = (uint32_t)(it / NBUF);
-        if (use > 0 && !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1))
+        if (use > 0 &&
+            !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1, LIM))
           return false;
         Meta m;
         m.inst = b; m.o = o; m.in = in; m.flags = flags; m.slot = slot;
@@ -361,6 +363,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         const uint32_t fb = smem_u32(&full[buf]);
         if (flags & META_END) {
           mbar_arrive(fb);
+        } else if (p.hold > 0 && i == 0 && it == p.hold - 1) {
+          // test of the time-out path: this stage's arrival is never signalled and no copy
+          // is issued for it, so every wait on it runs out after LIM cycles
         } else {
           const InstDesc& d = desc(b);
           mbar_arrive_expect_tx(fb, SM::B_BYTES + (STORED ? 0u : col_bytes + 1024u));
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         const int buf = (int)(k % NBUF);
         long long t0 = clock64();
         while (!mbar_try_wait(smem_u32(&full[buf]), (uint32_t)(k / NBUF) & 1u)) {
-          if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+          if (clock64() - t0 > LIM) {
             atomicCAS(p.err, 0, 9);
             break;
           }
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       bool ok = true;
       for (;; ++it) {
         const int buf = (int)(it % NBUF);
-        if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2)) {
+        if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2, LIM)) {
           ok = false;
           break;
         }
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         const bool seg_last = (flags & META_LAST) || ((run_pos + 1) % F == 0);
         ++run_pos;
         if (seg_first && seg > 0) {
-          if (!mbar_wait(smem_u32(aempty), (uint32_t)(seg - 1) & 1u, abort_flag, p.err, 3)) {
+          if (!mbar_wait(smem_u32(aempty), (uint32_t)(seg - 1) & 1u, abort_flag, p.err, 3, LIM)) {
             ok = false;
             break;
           }
@@ -445,7 +450,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         for (int st = 0; st < 2; ++st, ++gstage) {
           const int slot = (int)(gstage % SM::NSLOT);
           if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / SM::NSLOT) & 1u, abort_flag,
-                         p.err, 4)) {
+                         p.err, 4, LIM)) {
             ok = false;
             break;
           }
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       tc_commit(smem_u32(drain));
       long long t0 = clock64();
       while (!mbar_try_wait(smem_u32(drain), 0u)) {
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+        if (clock64() - t0 > LIM) {
           atomicCAS(p.err, 0, 10);
           break;
         }
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     // the run's output and clear the running sums.
     auto drain = [&]() -> bool {
       drain_due = false;
-      if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7)) return false;
+      if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7, LIM)) return false;
       tc_fence_after();
       float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
       const uint32_t lb = tmem + lane_base;
@@ -581,13 +586,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         // combine the four warpgroups' coil ranges through shared memory (bounded
         // mbarrier waits, no unbounded named barrier)
         if (run > 0 &&
-            !warp_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8))
+            !warp_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8, LIM))
           return false;
         sRed[g * 128 + row] = acc;
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(ered));
         if (g == 0) {
-          if (!warp_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8)) return false;
+          if (!warp_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8, LIM)) return false;
           float2 v = sRed[row];
           for (int k = 1; k < 4; ++k) {
             v.x += sRed[k * 128 + row].x;
@@ -605,7 +610,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     };
     for (;; ++it) {
       const int buf = (int)(it % NBUF);
-      if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5)) {
+      if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5, LIM)) {
         ok = false;
         break;
       }
@@ -634,7 +639,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         const int slot = (int)(gstage % SM::NSLOT);
         if (gstage >= SM::NSLOT &&
             !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / SM::NSLOT - 1) & 1u,
-                       abort_flag, p.err, 6)) {
+                       abort_flag, p.err, 6, LIM)) {
           ok = false;
           break;
         }
@@ -760,6 +765,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       ok = drain();
     }
     if (ok) flush_pending();
+    // after a time-out, stores of the stage in progress may still be in flight: complete
+    // them before the tensor memory is released
+    tmem_st_wait();
     (void)ok;
   }
 
@@ -1164,6 +1172,8 @@ static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, co
   prm.err = P->tc_err;
   prm.stop = stop;
   prm.seg_len = P->tc_seg_len;
+  prm.wait_limit = P->tc_wait_cycles;
+  prm.hold = P->tc_test_hold;
   const int G = P->tc_grid;
   return tc_launch(P, mode, npart, P->Cp, P->RT, prm, G, st, d.stored != nullptr);
 }

@@ -44,6 +44,8 @@ struct Params {
   int* err;              // device error word (nonzero after a time-out)
   const double* stop;    // stream-K: CG stop flag (nullable)
   int seg_len;           // accumulator drain interval (pairs of 128 x 128)
+  long long wait_limit;  // bounded waits give up after this many SM cycles (0: ~2 s)
+  int hold;              // tests only: > 0 makes CTA 0's loader withhold stage hold - 1
 };
 
 // Per-stage metadata passed from the loader to the MMA and generator warps.

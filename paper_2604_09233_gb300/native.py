@@ -55,7 +55,8 @@ KERNEL_CLASSES = ["tc_encode_pass", "tc_adjoint_pass", "fp32_encode", "fp32_adjo
 
 class Tuning(ctypes.Structure):
     _fields_ = [("seg_len", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("wait_limit_us", ctypes.c_int32), ("test_hold_stage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class _Problem(ctypes.Structure):
@@ -67,7 +68,7 @@ class _Problem(ctypes.Structure):
 class CGOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("rel_tol", ctypes.c_double), ("refine_every", ctypes.c_int32),
-                ("apply_j", ctypes.c_int32)]
+                ("apply_j", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
 
 
 class SmoothOpts(ctypes.Structure):
@@ -241,12 +242,12 @@ def sense_normal_op(plan, prec, m, out, stream=None):
 
 
 def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refine_every=0,
-                   apply_j=True, history=True, stream=None):
-    """Returns (info dict, history array [iters+1][3] or None)."""
+                   apply_j=True, history=True, stream=None, use_x0=False):
+    """Returns (info dict, history array [iters+1][3] or None). use_x0: x holds the start."""
     ps, ks, ss = _ptr(s)
     px, kx, sx = _ptr(x)
     opts = CGOpts(int(max_iter), int(prec), float(rel_tol), int(refine_every),
-                  1 if apply_j else 0)
+                  1 if apply_j else 0, 1 if use_x0 else 0)
     info = CGInfo()
     hist = np.full((int(max_iter) + 1, 3), np.nan) if history else None
     _check(_lib.sense_cg_solve(plan, ps, px, ctypes.byref(opts),
@@ -257,13 +258,13 @@ def sense_cg_solve(plan, s, x, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refi
 
 
 def sense_cg_solve_iterates(plan, s, iterates, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0,
-                            refine_every=0, apply_j=True, stream=None):
-    """CG recording every iterate into iterates ([max_iter+1][L] complex64 CUDA tensor).
-    Returns (info dict, history array [iters+1][3])."""
+                            refine_every=0, apply_j=True, stream=None, use_x0=False):
+    """CG recording every iterate into iterates ([max_iter+1][L] complex64 CUDA tensor;
+    with use_x0 row 0 holds the start on input). Returns (info dict, history [iters+1][3])."""
     ps, _, ss = _ptr(s)
     pX, _, sX = _ptr(iterates)
     opts = CGOpts(int(max_iter), int(prec), float(rel_tol), int(refine_every),
-                  1 if apply_j else 0)
+                  1 if apply_j else 0, 1 if use_x0 else 0)
     info = CGInfo()
     hist = np.full((int(max_iter) + 1, 3), np.nan)
     _check(_lib.sense_cg_solve_iterates(plan, ps, pX, ctypes.byref(opts), hist.ctypes.data,
@@ -410,7 +411,7 @@ def sense_cg_solve_ckpt(plan, s, x, ckpt, max_iter, ckpt_every, prec=SENSE_PREC_
     ps, _, ss = _ptr(s)
     px, _, sx = _ptr(x)
     pc, kc, _ = _ptr(ckpt, np.uint8)
-    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), 0, 1 if apply_j else 0)
+    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), 0, 1 if apply_j else 0, 0)
     info = CGInfo()
     _check(_lib.sense_cg_solve_ckpt(plan, ps, px, ctypes.byref(opts), int(ckpt_every), pc,
                                     int(kc.numel()), ctypes.byref(info),
@@ -484,7 +485,7 @@ def sense_batch_cg_solve(batch, s_list, x_list, max_iter, prec=SENSE_PREC_TC_SPL
                          apply_j=True, stream=None):
     """CG for every instance (device tensors); returns the list of info dicts."""
     n = len(s_list)
-    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), 0, 1 if apply_j else 0)
+    opts = CGOpts(int(max_iter), int(prec), float(rel_tol), 0, 1 if apply_j else 0, 0)
     infos = (CGInfo * n)()
     st = stream if stream is not None else _ptr(s_list[0])[2]
     _check(_lib.sense_batch_cg_solve(batch, _ptr_array(s_list), _ptr_array(x_list),
@@ -561,11 +562,12 @@ def sense_plan_sync(plan, stream=None):
 def sense_plan_get_tuning(plan):
     t = Tuning()
     _check(_lib.sense_plan_get_tuning(plan, ctypes.byref(t)), "sense_plan_get_tuning")
-    return {"seg_len": t.seg_len, "grid": t.grid}
+    return {"seg_len": t.seg_len, "grid": t.grid, "wait_limit_us": t.wait_limit_us,
+            "test_hold_stage": t.test_hold_stage}
 
 
-def sense_plan_set_tuning(plan, seg_len=8, grid=0):
-    t = Tuning(int(seg_len), int(grid))
+def sense_plan_set_tuning(plan, seg_len=4, grid=0, wait_limit_us=0, test_hold_stage=0):
+    t = Tuning(int(seg_len), int(grid), int(wait_limit_us), int(test_hold_stage))
     _check(_lib.sense_plan_set_tuning(plan, ctypes.byref(t)), "sense_plan_set_tuning")
 
 
@@ -653,10 +655,16 @@ class Plan:
         sense_plan_sync(self.handle)
         return out
 
-    def cg(self, s, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refine_every=0, apply_j=True):
+    def cg(self, s, max_iter, prec=SENSE_PREC_FP32, rel_tol=0.0, refine_every=0, apply_j=True,
+           x0=None):
+        """CG from rho = 0, or from x0 ([L] complex64 tensor, the start before the final
+        multiplication by j) when given."""
         import torch
-        x = torch.empty((self.L,), dtype=torch.complex64, device=s.device)
+        if x0 is None:
+            x = torch.empty((self.L,), dtype=torch.complex64, device=s.device)
+        else:
+            x = x0.detach().to(device=s.device, dtype=torch.complex64).clone().contiguous()
         info, hist = sense_cg_solve(self.handle, s, x, max_iter, prec, rel_tol, refine_every,
-                                    apply_j)
+                                    apply_j, use_x0=x0 is not None)
         sense_plan_sync(self.handle)
         return x, info, hist

@@ -98,19 +98,18 @@ def test_host_pointers_match_device(case):
     assert np.array_equal(m_host, plan.adjoint(_t(s_host, dev)).cpu().numpy())
 
 
-# CG parity at equal iteration count is meaningful only where single-precision CG can
-# track FP64 CG: the B0-only case (no spatial encoding beyond off-resonance) and the tiny
-# fully sampled cases are so ill-conditioned that any FP32 CG departs from the FP64 one
-# within a few iterations. They are operator-parity cases only.
-OPERATOR_ONLY = {"b0_only", "small_16_32_600_o2", "small_12_64_300_o3", "small_6_1_100_o1"}
+# How long single-precision CG tracks FP64 CG iterate by iterate depends on the conditioning
+# (FP64 CG itself departs from FP64 CG under 1e-7 product noise within 10-15 iterations on
+# this family: tests/test_cg_sensitivity.py). The B0-only case (no spatial encoding beyond
+# off-resonance) and the tiny fully sampled cases are compared after 5 iterations, the others
+# after 10.
+EARLY = {"b0_only", "small_16_32_600_o2", "small_12_64_300_o3", "small_6_1_100_o1"}
 
 
 def test_cg_equal_iteration_count(case):
     wl, plan, dev = case
-    if wl.name in OPERATOR_ONLY:
-        pytest.skip("operator-parity-only case")
     sigma = (oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j) + wl.noise).astype(np.complex64)
-    n_it = 10
+    n_it = 5 if wl.name in EARLY else 10
     x, info, hist = plan.cg(_t(sigma, dev), n_it)
     ref = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), n_it, j=wl.j, history=True)
     assert info["iters"] == n_it and info["status"] == 0
@@ -125,15 +124,16 @@ def test_cg_equal_iteration_count(case):
 
 def test_cg_relative_tolerance(case):
     wl, plan, dev = case
-    if wl.name in OPERATOR_ONLY:
-        pytest.skip("operator-parity-only case")
     sigma = (oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j) + wl.noise).astype(np.complex64)
     ref = oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), 40, j=wl.j, history=True)
     r = ref["history"][:, 0]
-    tol = float(np.sqrt(r[3] * r[4]) / r[0])       # between iterations 3 and 4
+    # the threshold sits in the largest residual drop among iterations 2..6, so that the
+    # stop iteration is the same for any iterate within single-precision reach of FP64
+    n = 2 + int(np.argmax(r[2:6] / r[3:7]))
+    tol = float(np.sqrt(r[n] * r[n + 1]) / r[0])   # between iterations n and n + 1
     x, info, _ = plan.cg(_t(sigma, dev), 40, rel_tol=tol)
-    assert info["iters"] == 4
-    assert _rel(x.cpu().numpy(), oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), 4,
+    assert info["iters"] == n + 1
+    assert _rel(x.cpu().numpy(), oracle.cg(wl.Kmat, wl.Rmat, wl.S, sigma.astype(complex), n + 1,
                                            j=wl.j)["x"]) <= TOL_CG
 
 

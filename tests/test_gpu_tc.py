@@ -77,18 +77,14 @@ def test_tc_normal(case, prec):
     assert _rel(q, ref) <= TOL[prec]
 
 
-CG_CASES = {"small_24_8_1500_o3", "small_20_5_1000_o1", "small_40_16_5000_o3"}
-
-
 def test_tc_split_cg_equal_iteration_count(case):
-    """Early iterations: the split tensor-core CG iterate equals the FP64 one within 1e-4.
-    Deeper, FP64 CG itself moves by ~1e-2 under any single-precision perturbation of the
-    matrix-vector products (measured: 1e-7 operator noise or FP32 rounding of the CG
-    vectors alone), so there the check is on what the iterate is for: its distance to the
-    ground-truth image must agree with FP64 CG's to 1%."""
+    """Early iterations (5): the split tensor-core CG iterate equals the FP64 one within 1e-4,
+    for every case (1 to 64 coils). Deeper, FP64 CG itself moves by 1e-4..1e-2 under product
+    noise of the split operator's size (3e-6; tests/test_cg_sensitivity.py measures the
+    effect), so at 10 iterations the check is on what the iterate is for: its distance to the
+    ground-truth image must agree with FP64 CG's to 2% (5% for the one-coil 6x6 case, whose 36
+    unknowns are the worst conditioned here)."""
     wl, plan, dev = case
-    if wl.name not in CG_CASES:
-        pytest.skip("operator-parity-only case (too ill-conditioned for FP32-level CG parity)")
     sigma = (oracle.encode(wl.Kmat, wl.Rmat, wl.S, wl.m_true, j=wl.j) + wl.noise).astype(np.complex64)
     n_early, n_deep = 5, 10
     x, info, _ = plan.cg(_t(sigma, dev), n_early, prec=SPLIT)
@@ -100,7 +96,8 @@ def test_tc_split_cg_equal_iteration_count(case):
     truth = wl.m_true * (wl.j if wl.j is not None else 1.0)
     e_gpu = _rel(x.cpu().numpy(), truth)
     e_ref = _rel(ref["x"], truth)
-    assert abs(e_gpu - e_ref) <= 1e-2 * e_ref
+    print(f"{wl.name}: 10 it. to truth {e_gpu:.5f} vs FP64 {e_ref:.5f}")
+    assert abs(e_gpu - e_ref) <= (5e-2 if wl.C == 1 else 2e-2) * e_ref
 
 
 def test_tc_results_are_deterministic(case):
