@@ -9,6 +9,7 @@
 // writes the caller's output, and keeps its only scratch -- the per-split partial sums of
 // the FP32 encode kernel -- in a fixed array owned by the library.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "sense_internal.cuh"
@@ -16,8 +17,9 @@
 namespace sense {
 namespace noalloc {
 
-// Partial sums [nsplit][K][CP] complex64: 16 MiB. Every GPU that loads the library holds
-// it until the process exits. Calls share it; calls that overlap on the GPU race.
+// Partial sums [nsplit][K][CP] complex64: 16 MiB. The device code is loaded lazily, so the
+// array is created on a device by the first call there; from then on that device holds it
+// until the process exits. Calls share it; calls that overlap on the GPU race.
 constexpr size_t SCRATCH_FLOAT2 = (size_t)1 << 21;
 static __device__ __align__(256) float2 g_scratch[SCRATCH_FLOAT2];
 
@@ -104,21 +106,24 @@ __global__ void reduce_kernel(const float2* __restrict__ part, int nsplit, int64
 }
 
 // Device address of the scratch array, looked up once per device (cudaGetSymbolAddress
-// with that device current); a host-side name of a __device__ array is not a device
-// address and must never be passed to a kernel.
+// with that device current, which also loads this file's device code there) and cached for
+// the life of the process (it does not survive cudaDeviceReset); a host-side name of a
+// __device__ array is not a device address and must never be passed to a kernel.
 constexpr int MAX_DEVICES = 64;
-static float2* g_scratch_ptr[MAX_DEVICES] = {nullptr};
+static std::atomic<float2*> g_scratch_ptr[MAX_DEVICES];
 
 static int scratch_for_current_device(float2** out) {
   int dev = 0;
   SENSE_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return set_error(SENSE_EUNSUPPORTED, "device ordinal >= 64");
-  if (!g_scratch_ptr[dev]) {
+  float2* ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
     void* p = nullptr;
     SENSE_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch));
-    g_scratch_ptr[dev] = (float2*)p;
+    ptr = (float2*)p;
+    g_scratch_ptr[dev].store(ptr, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = ptr;
   return SENSE_OK;
 }
 
