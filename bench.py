@@ -41,7 +41,8 @@ def _parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tc_fp16", "tc_split"])
     ap.add_argument("--workload", default="target_256",
-                    choices=["target_256", "precision_128", "plain_32", "stack_3d", "batch_64"])
+                    choices=["target_256", "precision_128", "plain_32", "stack_3d", "batch_64",
+                             "batch_small_64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true",
                     help="skip the (untimed) differentiation measurements")
@@ -188,7 +189,7 @@ def run_reference_batch(args):
     """Oracle on the batch mix: its voxel-sample-coil rate measured on a bounded sample of
     every 8th instance, converted to applies/s over the mix of all instances."""
     from paper_2604_09233_gb300 import synthetic
-    wls = synthetic.batch_64()
+    wls = getattr(synthetic, args.workload)()
     per_step = max(2.0, 100.0 / max(1, args.steps + args.warmup))
     sample = wls[::8]
 
@@ -213,7 +214,7 @@ def run_reference_batch(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batch_64_2d_uneven", "instances": len(wls)},
+        "config": {"workload": BATCH_WORKLOADS[args.workload], "instances": len(wls)},
         "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "value": value, "unit": UNIT,
                          "sample": f"E and E^H row/voxel samples of {len(sample)} of the "
                                    f"{len(wls)} instances, FP64, rate converted to the mix"},
@@ -226,7 +227,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload == "batch_64":
+    if args.workload in BATCH_WORKLOADS:
         return run_reference_batch(args)
     wl = _workload(args.workload)
     per_step = max(2.0, 100.0 / max(1, args.steps + args.warmup))
@@ -281,9 +282,9 @@ KERNEL_TRAFFIC = {
 
 
 def pass_kernel_source_hash():
-    """SHA-256 of the pass kernel's code: sense_tc.cu up to the end of tc_pass_kernel (its
-    helpers and the kernel itself) followed by sense_tc.cuh, with // comments and blank lines
-    removed (they do not change the compiled kernel)."""
+    """SHA-256 of the generated-tile pass kernel's code: sense_tcp.cu up to its launch helpers
+    (the layout, the kernel and everything before it), then sense_ptx.cuh and sense_tc.cuh,
+    with // comments and blank lines removed (they do not change the compiled kernel)."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2604_09233_gb300", "csrc")
@@ -292,12 +293,13 @@ def pass_kernel_source_hash():
         lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
         return "\n".join(ln for ln in lines if ln.strip()).encode()
 
-    with open(os.path.join(csrc, "sense_tc.cu")) as fh:
+    with open(os.path.join(csrc, "sense_tcp.cu")) as fh:
         text = fh.read()
-    end = text.index("template <int CP, int RP, int NPART>\nconstexpr size_t smem_bytes()")
+    end = text.index("template <int MODE, int CP, int NPART, int NKP>\nstatic int launch(")
     h = hashlib.sha256(code(text[:end]))
-    with open(os.path.join(csrc, "sense_tc.cuh")) as fh:
-        h.update(code(fh.read()))
+    for name in ("sense_ptx.cuh", "sense_tc.cuh"):
+        with open(os.path.join(csrc, name)) as fh:
+            h.update(code(fh.read()))
     return h.hexdigest()
 
 
@@ -640,9 +642,14 @@ def run_ours(args):
 BATCH_METRIC = "E^H E applies/s summed over instances (batched CG, uneven instances)"
 
 
+BATCH_WORKLOADS = {"batch_64": "batch_64_2d_uneven", "batch_small_64": "batch_64_2d_small"}
+
+
 def run_batch(args):
     """64 independent uneven 2D instances solved by one batched CG (per-instance stop at
-    relative residual 1e-3, at most 50 iterations). A step is one sense_batch_cg_solve."""
+    relative residual 1e-3, at most 50 iterations). A step is one sense_batch_cg_solve.
+    batch_64: matrices {64..256}^2 (most instances fill the GPU alone); batch_small_64:
+    matrices {64, 96}^2 with 4096-8192 samples, where one instance underfills 152 SMs."""
     import torch
     from paper_2604_09233_gb300 import native, synthetic
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
@@ -651,7 +658,7 @@ def run_batch(args):
     torch.cuda.set_device(dev)
     prec_name = "tc_split" if args.prec == "auto" else args.prec
     prec = native.PRECISIONS[prec_name]
-    wls = synthetic.batch_64()
+    wls = getattr(synthetic, args.workload)()
     t0 = time.perf_counter()
     batch = native.Batch([(w.Kmat, w.Rmat, w.S, w.j) for w in wls])
     t_create = time.perf_counter() - t0
@@ -726,11 +733,12 @@ def run_batch(args):
     sincos_peak = native.sense_diag_sincos_rate(300.0)
     achieved = pairs / (tune["ms"] / 1e3)
     n = len(wls)
+    clocks = clk.summary()
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": "batch_64_2d_uneven", "instances": n,
+        "config": {"workload": BATCH_WORKLOADS[args.workload], "instances": n,
                    "matrices": sorted({w.shape[0] for w in wls}),
                    "coils": sorted({w.C for w in wls}),
                    "samples": [min(w.K for w in wls), max(w.K for w in wls)],
@@ -764,7 +772,7 @@ def main():
         run_reference(args)
     elif args.op_only:
         run_op_only(args)
-    elif args.workload == "batch_64":
+    elif args.workload in BATCH_WORKLOADS:
         run_batch(args)
     else:
         run_ours(args)

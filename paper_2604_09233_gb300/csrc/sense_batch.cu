@@ -124,6 +124,11 @@ int build_layout(sense_batch_s* B) {
       e.n_outer = enc ? P->nsb : P->nvb;
       e.n_inner = enc ? P->nvb : P->nsb;
       e.chunk = CH;
+      e.rowPh = enc ? P->phK_row : P->phR_row;
+      e.colPh = enc ? P->phR_col : P->phK_col;
+      e.rowAncR = enc ? P->BancR : P->AancR;
+      e.colAncR = enc ? P->AancR : P->BancR;
+      e.ph_unscale = P->ph_unscale;
       e.stop = nullptr;
       d[m][0].push_back(e);
       e.stop = P->scal + SC_STOP;

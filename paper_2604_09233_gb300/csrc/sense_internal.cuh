@@ -77,6 +77,15 @@ struct sense_plan_s {
   float* dRt = nullptr;      // [nvb][RT][TILE]
   float* Aanc = nullptr;     // [nsb][Lp] frac(Kc . R(l))
   float* Banc = nullptr;     // [nvb][Kp] frac((K(k) - Kc) . Rc)
+  float* AancR = nullptr;    // the same two tables in radians, 2 pi frac(.)
+  float* BancR = nullptr;
+  // tensor-core phase operands (FP16 hi/lo images of the kept rows of dK and dR, scaled)
+  int nkp = 1;               // K-steps of 16 rows: 1 (RT <= 16) or 2
+  float ph_unscale = 1.0f;
+  uint8_t* phK_row = nullptr;  // [nsb][TCP_ROW_BYTES] samples as rows (E pass)
+  uint8_t* phR_row = nullptr;  // [nvb][TCP_ROW_BYTES] voxels as rows (E^H pass)
+  uint8_t* phR_col = nullptr;  // [nvb][tcp_col_bytes] voxels streamed (E pass)
+  uint8_t* phK_col = nullptr;  // [nsb][tcp_col_bytes] samples streamed (E^H pass)
   float2* S = nullptr;       // [Lp][Cp]  S o j, plan order
   float* jv = nullptr;       // [Lp] j in plan order (1 for padding)
   float* tk = nullptr;       // [Kp] K(:,0) = t_k as float (0 for padding)

@@ -10,6 +10,8 @@
 //   the local bilinear term D, whose size is bounded by the extent of one block in k and
 //   in r, is evaluated per pair in FP32. Rows of K R that are constant inside every block
 //   (or zero) contribute nothing to D and are dropped from it.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -86,20 +88,27 @@ static void kd_order(std::vector<int32_t>& idx, int64_t lo, int64_t hi, const do
 // FP64 anchor kernels.
 // --------------------------------------------------------------------------------------
 __device__ __forceinline__ float frac_turns(double v) { return (float)(v - rint(v)); }
+__device__ __forceinline__ float frac_radians(double v) {
+  return (float)(6.283185307179586 * (v - rint(v)));
+}
 
+// A(b, l) = frac(Kc(b) . R(l)), in turns (A) and in radians (AR)
 __global__ void anchors_A_kernel(const double* __restrict__ Kc, const double* __restrict__ Rd,
-                                 float* __restrict__ A, int P1, int64_t Lp) {
+                                 float* __restrict__ A, float* __restrict__ AR, int P1,
+                                 int64_t Lp) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = blockIdx.y;
   if (l >= Lp) return;
   double acc = 0.0;
   for (int p = 0; p < P1; ++p) acc = fma(Kc[(int64_t)sb * P1 + p], Rd[(int64_t)p * Lp + l], acc);
   A[(int64_t)sb * Lp + l] = frac_turns(acc);
+  AR[(int64_t)sb * Lp + l] = frac_radians(acc);
 }
 
+// B(v, k) = frac((K(k) - Kc(b(k))) . Rc(v)), in turns (B) and in radians (BR)
 __global__ void anchors_B_kernel(const double* __restrict__ Kd, const double* __restrict__ Kc,
-                                 const double* __restrict__ Rc, float* __restrict__ B, int P1,
-                                 int64_t Kp) {
+                                 const double* __restrict__ Rc, float* __restrict__ B,
+                                 float* __restrict__ BR, int P1, int64_t Kp) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int vb = blockIdx.y;
   if (k >= Kp) return;
@@ -108,6 +117,111 @@ __global__ void anchors_B_kernel(const double* __restrict__ Kd, const double* __
   for (int p = 0; p < P1; ++p)
     acc = fma(Kd[k * P1 + p] - Kc[sb * P1 + p], Rc[(int64_t)vb * P1 + p], acc);
   B[(int64_t)vb * Kp + k] = frac_turns(acc);
+  BR[(int64_t)vb * Kp + k] = frac_radians(acc);
+}
+
+// ---------------------------------------------------------------------------------------
+// Operand images of the local bilinear phase for the tensor-core phase kernel. With the
+// kept rows q, the phase in radians is D(k,l) = 2 pi sum_q dK(k,q) dR(l,q). Per row q a
+// power of two u_q balances the two factors, and one more power of two S scales both so
+// that the largest entry is below 2^12: kv = dK u_q S, rv = dR 2 pi / u_q S, D = (kv . rv) /
+// S^2. Each value is split into FP16 hi = fp16(v) and lo = fp16(v - hi). An image row holds
+// 64 FP16 (128 bytes) in the 128B-swizzled K-major layout of the MMA operands (16-byte chunk
+// c of row n at n * 128 + (c ^ (n & 7)) * 16): FP16 h = part * 16 nkp + q of row n, part 0 =
+// hi, 1 = lo. The row-side image of a block lists its 128 entities in order. The streamed-side
+// image lists each 64-wide stage's entities in the order the generator warps read the phases
+// back from tensor memory: MMA row n < 32 is element 16 (n / 8) + n % 8, n >= 32 is element
+// 16 ((n - 32) / 8) + 8 + (n - 32) % 8; for nkp = 1 both stages share 64 rows (stage st in
+// FP16 32 st + h), for nkp = 2 each stage has its own 64 rows (8 KB).
+// ---------------------------------------------------------------------------------------
+static inline size_t ph_off(int64_t n, int h) {
+  return (size_t)n * 128 + (size_t)((((h >> 3) ^ (int)(n & 7))) << 4) + (size_t)(h & 7) * 2;
+}
+
+// hi / lo FP16 parts of v at FP16 positions h (hi) and h + 16 nkp (lo) of image row n
+static void ph_put(uint8_t* img, int64_t n, int h, int nkp, double v) {
+  const __half hi = __double2half(v);
+  const __half lo = __double2half(v - (double)__half2float(hi));
+  std::memcpy(img + ph_off(n, h), &hi, 2);
+  std::memcpy(img + ph_off(n, h + 16 * nkp), &lo, 2);
+}
+
+// MMA row of streamed element j (0..63) of a stage
+static inline int ph_perm_row(int j) {
+  const int g = j >> 4, e = j & 15;
+  return e < 8 ? 8 * g + e : 32 + 8 * g + (e - 8);
+}
+
+template <typename T>
+static int dalloc(T** p, size_t n);
+
+static int build_phase_images(sense_plan_s* P, const std::vector<double>& Kt,
+                              const std::vector<double>& Kc, const std::vector<double>& Rd,
+                              const std::vector<double>& Rc, cudaStream_t st) {
+  const int P1 = P->P1, r = P->r;
+  const int64_t Kp = P->Kp, Lp = P->Lp;
+  const int nkp = P->RT <= 16 ? 1 : 2;
+  P->nkp = nkp;
+  const int colb = tc::tcp_col_bytes(nkp);
+  std::vector<double> mk(std::max(1, r), 0.0), mr(std::max(1, r), 0.0);
+  auto dk = [&](int64_t k, int q) {
+    return Kt[(size_t)k * P1 + P->rows[q]] - Kc[(size_t)(k / TILE) * P1 + P->rows[q]];
+  };
+  auto dr = [&](int64_t i, int q) {
+    return Rd[(size_t)P->rows[q] * Lp + i] - Rc[(size_t)(i / TILE) * P1 + P->rows[q]];
+  };
+  for (int q = 0; q < r; ++q) {
+    for (int64_t k = 0; k < Kp; ++k) mk[q] = std::max(mk[q], std::fabs(dk(k, q)));
+    for (int64_t i = 0; i < Lp; ++i) mr[q] = std::max(mr[q], std::fabs(dr(i, q)));
+  }
+  const double two_pi = 2.0 * M_PI;
+  std::vector<double> u(std::max(1, r), 1.0);
+  double vmax = 0.0;
+  for (int q = 0; q < r; ++q) {
+    if (mk[q] > 0.0 && mr[q] > 0.0)
+      u[q] = std::ldexp(1.0, (int)std::lround(0.5 * std::log2(two_pi * mr[q] / mk[q])));
+    vmax = std::max(vmax, std::max(mk[q] * u[q], two_pi * mr[q] / u[q]));
+  }
+  const double S = vmax > 0.0 ? std::ldexp(1.0, (int)std::floor(std::log2(4096.0 / vmax))) : 1.0;
+  P->ph_unscale = (float)(1.0 / (S * S));
+  std::vector<uint8_t> kr((size_t)P->nsb * tc::TCP_ROW_BYTES, 0), kc((size_t)P->nsb * colb, 0);
+  std::vector<uint8_t> rr((size_t)P->nvb * tc::TCP_ROW_BYTES, 0), rc((size_t)P->nvb * colb, 0);
+  for (int64_t k = 0; k < Kp; ++k) {
+    const int64_t b = k / TILE, j = k % TILE;
+    const int st = (int)(j >> 6), n = ph_perm_row((int)(j & 63));
+    for (int q = 0; q < r; ++q) {
+      const double v = dk(k, q) * u[q] * S;
+      ph_put(kr.data() + (size_t)b * tc::TCP_ROW_BYTES, j, q, nkp, v);
+      if (nkp == 1)
+        ph_put(kc.data() + (size_t)b * colb, n, 32 * st + q, 1, v);
+      else
+        ph_put(kc.data() + (size_t)b * colb + (size_t)st * 8192, n, q, 2, v);
+    }
+  }
+  for (int64_t i = 0; i < Lp; ++i) {
+    const int64_t b = i / TILE, j = i % TILE;
+    const int st = (int)(j >> 6), n = ph_perm_row((int)(j & 63));
+    for (int q = 0; q < r; ++q) {
+      const double v = dr(i, q) * (two_pi / u[q]) * S;
+      ph_put(rr.data() + (size_t)b * tc::TCP_ROW_BYTES, j, q, nkp, v);
+      if (nkp == 1)
+        ph_put(rc.data() + (size_t)b * colb, n, 32 * st + q, 1, v);
+      else
+        ph_put(rc.data() + (size_t)b * colb + (size_t)st * 8192, n, q, 2, v);
+    }
+  }
+  int rc_ = SENSE_OK;
+  if ((rc_ = dalloc(&P->phK_row, kr.size())) != SENSE_OK) return rc_;
+  if ((rc_ = dalloc(&P->phK_col, kc.size())) != SENSE_OK) return rc_;
+  if ((rc_ = dalloc(&P->phR_row, rr.size())) != SENSE_OK) return rc_;
+  if ((rc_ = dalloc(&P->phR_col, rc.size())) != SENSE_OK) return rc_;
+  SENSE_CUDA_TRY(cudaMemcpyAsync(P->phK_row, kr.data(), kr.size(), cudaMemcpyHostToDevice, st));
+  SENSE_CUDA_TRY(cudaMemcpyAsync(P->phK_col, kc.data(), kc.size(), cudaMemcpyHostToDevice, st));
+  SENSE_CUDA_TRY(cudaMemcpyAsync(P->phR_row, rr.data(), rr.size(), cudaMemcpyHostToDevice, st));
+  SENSE_CUDA_TRY(cudaMemcpyAsync(P->phR_col, rc.data(), rc.size(), cudaMemcpyHostToDevice, st));
+  // the host vectors die at return
+  SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+  return SENSE_OK;
 }
 
 __global__ void deltas_kernel(const double* __restrict__ Kd, const double* __restrict__ Kc,
@@ -157,6 +271,10 @@ static void free_geometry(sense_plan_s* P) {
   cudaFree(P->dKd); cudaFree(P->dRd); cudaFree(P->dKc); cudaFree(P->dRc);
   cudaFree(P->drows); cudaFree(P->dK); cudaFree(P->dR); cudaFree(P->Aanc); cudaFree(P->Banc);
   cudaFree(P->dKt); cudaFree(P->dRt);
+  cudaFree(P->AancR); cudaFree(P->BancR);
+  cudaFree(P->phK_row); cudaFree(P->phK_col); cudaFree(P->phR_row); cudaFree(P->phR_col);
+  P->AancR = P->BancR = nullptr;
+  P->phK_row = P->phK_col = P->phR_row = P->phR_col = nullptr;
   P->dKt = P->dRt = nullptr;
   P->dKd = P->dRd = P->dKc = P->dRc = nullptr;
   P->drows = nullptr;
@@ -247,6 +365,8 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   SENSE_TRY(dalloc(&P->dRt, (size_t)Lp * P->RT));
   SENSE_TRY(dalloc(&P->Aanc, (size_t)P->nsb * Lp));
   SENSE_TRY(dalloc(&P->Banc, (size_t)P->nvb * Kp));
+  SENSE_TRY(dalloc(&P->AancR, (size_t)P->nsb * Lp));
+  SENSE_TRY(dalloc(&P->BancR, (size_t)P->nvb * Kp));
   SENSE_CUDA_TRY(cudaMemcpyAsync(P->dKd, Kt.data(), Kt.size() * 8, cudaMemcpyHostToDevice, st));
   SENSE_CUDA_TRY(cudaMemcpyAsync(P->dRd, Rd.data(), Rd.size() * 8, cudaMemcpyHostToDevice, st));
   SENSE_CUDA_TRY(cudaMemcpyAsync(P->dKc, Kc.data(), Kc.size() * 8, cudaMemcpyHostToDevice, st));
@@ -254,11 +374,11 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   if (P->r > 0)
     SENSE_CUDA_TRY(cudaMemcpyAsync(P->drows, rows.data(), rows.size() * sizeof(int),
                                    cudaMemcpyHostToDevice, st));
-  anchors_A_kernel<<<dim3((unsigned)((Lp + 255) / 256), P->nsb), 256, 0, st>>>(P->dKc, P->dRd,
-                                                                               P->Aanc, P1, Lp);
+  anchors_A_kernel<<<dim3((unsigned)((Lp + 255) / 256), P->nsb), 256, 0, st>>>(
+      P->dKc, P->dRd, P->Aanc, P->AancR, P1, Lp);
   SENSE_CUDA_TRY(cudaGetLastError());
   anchors_B_kernel<<<dim3((unsigned)((Kp + 255) / 256), P->nvb), 256, 0, st>>>(
-      P->dKd, P->dKc, P->dRc, P->Banc, P1, Kp);
+      P->dKd, P->dKc, P->dRc, P->Banc, P->BancR, P1, Kp);
   SENSE_CUDA_TRY(cudaGetLastError());
   const int64_t nmax = std::max(Kp, Lp);
   deltas_kernel<<<(unsigned)((nmax + 255) / 256), 256, 0, st>>>(
@@ -267,7 +387,7 @@ static int build_geometry(sense_plan_s* P, cudaStream_t st) {
   SENSE_CUDA_TRY(cudaGetLastError());
   // the host vectors above die at return: make the copies complete first
   SENSE_CUDA_TRY(cudaStreamSynchronize(st));
-  return SENSE_OK;
+  return build_phase_images(P, Kt, Kc, Rd, Rc, st);
 }
 
 static int upload_sens(sense_plan_s* P, cudaStream_t st) {

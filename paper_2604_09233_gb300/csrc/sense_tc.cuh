@@ -24,6 +24,15 @@ struct InstDesc {
   // stored phase tiles (stored-P mode): per (row block, streamed block) pair 16 chunks
   // (stage, warpgroup, half) of [4 matrices: re hi, re lo, im hi, im lo][128 rows][8 FP16]
   const uint4* stored;
+  // tensor-core phase (sense_tcp.cu): FP16 hi/lo operand images of the local bilinear phase,
+  // 128B-swizzled K-major: the row side [n_outer][128 rows][128 B] in natural order and the
+  // streamed side [n_inner][TCP_COL_BYTES] in the permuted stage order; anchors in radians.
+  const uint8_t* rowPh;
+  const uint8_t* colPh;
+  const float* rowAncR;  // [n_inner][rows_total] radians
+  const float* colAncR;  // [n_outer][cols_total] radians
+  float ph_unscale;      // the phase images' products are radians times 1 / ph_unscale
+  int pad2;
 };
 
 // Two schedules feed the same kernel:
@@ -46,6 +55,8 @@ struct Params {
   int seg_len;           // accumulator drain interval (pairs of 128 x 128)
   long long wait_limit;  // bounded waits give up after this many SM cycles (0: ~2 s)
   int hold;              // tests only: > 0 makes CTA 0's loader withhold stage hold - 1
+  uint4* emit;           // tensor-core phase kernel, stream-K, split: also write the FP16
+                         // tiles it generates in the stored-P layout (nullable)
 };
 
 // Per-stage metadata passed from the loader to the MMA and generator warps.
@@ -60,9 +71,20 @@ enum Mode { ENC = 0, ADJ = 1 };
 }  // namespace tc
 
 // Launch one pass (template chosen by npart, cp = padded coils, rt = delta rows) on G CTAs;
-// stored: the phase tiles come from prm's descriptors' `stored` arrays.
+// stored: the phase tiles come from prm's descriptors' `stored` arrays. Up to 32 padded
+// coils the generated passes run the tensor-core phase kernel (sense_tcp.cu).
 int tc_launch(sense_plan_s* P, int mode, int npart, int cp, int rt, const tc::Params& prm, int G,
               cudaStream_t st, bool stored = false);
+namespace tc {
+// Tensor-core phase kernel (sense_tcp.cu): streamed-side image bytes per block for nkp
+// K-steps of 16 phase rows (nkp = 0: the stored-P variant, which reads its tiles from HBM),
+// the row-side bytes, whether it serves a launch, and the launch.
+constexpr int tcp_col_bytes(int nkp) { return nkp == 0 ? 0 : nkp == 1 ? 8192 : 16384; }
+constexpr int TCP_ROW_BYTES = 16384;
+bool tcp_covers(int cp, bool stored);
+int tcp_launch(sense_plan_s* P, int mode, int npart, int cp, int nkp, const Params& prm, int G,
+               cudaStream_t st);
+}  // namespace tc
 // Stored-P mode: generate (enable) or free the phase tiles of both passes.
 int tc_store_p(sense_plan_s* P, bool enable, cudaStream_t st);
 // B image of src (Y_int layout, nrows x Cp) or of S o pv; colmax computed unless have_colmax.

@@ -355,6 +355,26 @@ def batch_64(n=64, seed=5000):
     return out
 
 
+def batch_small_64(n=64, seed=6000):
+    """64 independent small 2D spiral instances, the case a persistent batched launch is for:
+    matrix uniform in {64, 96}^2, coils in {8, 16}, 4096-8192 samples at 2 us, R in {2, 3, 4},
+    B0 +-50..150 Hz, field expansion of order 1..3; stop at a relative residual of 1e-3 or 50
+    iterations. Instance i uses seed + i; the sizes are drawn with seed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        matrix = int(rng.choice([64, 96]))
+        coils = int(rng.choice([8, 16]))
+        samples = int(rng.integers(4096, 8193))
+        R = int(rng.choice([2, 3, 4]))
+        order = int(rng.integers(1, 4))
+        fmax = float(rng.uniform(50.0, 150.0))
+        out.append(make_spiral_2d(f"s{i}_{matrix}x{matrix}_{coils}c_{samples}s_o{order}",
+                                  seed + i, matrix, 0.22, coils, samples, 2e-6, R, fmax,
+                                  order=order, n_iter=50))
+    return out
+
+
 def small_batch(seed=7000):
     """Five small instances of uneven size for batch parity tests (ragged tiles, 1..32 coils,
     orders 1..3, one with intensity correction j)."""

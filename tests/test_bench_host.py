@@ -12,7 +12,7 @@ def _copy_sources(root):
     src = os.path.join(bench.ROOT, "paper_2604_09233_gb300", "csrc")
     dst = pathlib.Path(root) / "paper_2604_09233_gb300" / "csrc"
     dst.mkdir(parents=True)
-    for name in ("sense_tc.cu", "sense_tc.cuh"):
+    for name in ("sense_tcp.cu", "sense_ptx.cuh", "sense_tc.cuh"):
         shutil.copy(os.path.join(src, name), dst / name)
     return dst
 
@@ -21,13 +21,19 @@ def test_pass_kernel_hash_ignores_comments_but_not_code(repo_tmp, monkeypatch):
     dst = _copy_sources(repo_tmp)
     monkeypatch.setattr(bench, "ROOT", str(repo_tmp))
     h0 = bench.pass_kernel_source_hash()
-    f = dst / "sense_tc.cu"
+    f = dst / "sense_tcp.cu"
     text = f.read_text()
-    anchor = "__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {"
+    anchor = "__global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {"
     assert anchor in text
     f.write_text(text.replace(anchor, "// an added comment\n\n" + anchor + "  // trailing"))
     assert bench.pass_kernel_source_hash() == h0
-    f.write_text(text.replace("6.283185307179586f", "6.2831853f", 1))
+    f.write_text(text.replace("const uint16_t M1 = 0xBC00u;", "const uint16_t M1 = 0xBC01u;", 1))
+    assert bench.pass_kernel_source_hash() != h0
+    # the shared PTX wrappers are part of the kernel too
+    f.write_text(text)
+    w = dst / "sense_ptx.cuh"
+    wt = w.read_text()
+    w.write_text(wt.replace("(1024 >> 4) << 32", "(2048 >> 4) << 32", 1))
     assert bench.pass_kernel_source_hash() != h0
 
 
