@@ -44,7 +44,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait. Returns false (and raises the CTA abort flag and the global error word)
 // after `limit` SM clock cycles, or immediately once another thread has aborted.
-static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                        int* err, int site, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -60,6 +60,21 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
     }
   }
 }
+
+// Position in a ring of N mbarrier-guarded buffers: the index and the parity of the current
+// round, advanced without a division (a 64-bit division or modulo by a non-power of two costs
+// a warp tens of dependent instructions).
+template <int N>
+struct Ring {
+  int idx = 0;
+  uint32_t phase = 0;
+  __device__ __forceinline__ void next() {
+    if (++idx == N) {
+      idx = 0;
+      phase ^= 1u;
+    }
+  }
+};
 
 // Warp-uniform bounded wait: lane 0 polls, every lane gets the outcome and the warp is
 // converged on return (required before .sync.aligned tcgen05 instructions).

@@ -167,14 +167,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   if (warp == LOAD_WARP) {
     // ------------------------------------------------------------------ loader
     if (lane == 0) {
-      long long it = 0;
+      long long it = 0;   // blocks pushed
+      Ring<NBUF> rb;      // ring position of block it
       int run = 0;  // runs started: run r's row phase operand goes to ring slot r & 1
       bool ok = true;
       auto push = [&](int b, int o, int in, int flags, int slot) -> bool {
-        const int buf = (int)(it % NBUF);
-        const uint32_t use = (uint32_t)(it / NBUF);
-        if (use > 0 &&
-            !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1, LIM))
+        const int buf = rb.idx;
+        if (it >= NBUF &&
+            !mbar_wait(smem_u32(&empty[buf]), rb.phase ^ 1u, abort_flag, p.err, 1, LIM))
           return false;
         if (!STORED && !(flags & META_END) && (flags & META_FIRST)) {
           const int rs = run & 1;
@@ -213,17 +213,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
           }
         }
         ++it;
+        rb.next();
         return true;
       };
       if (!queue) {
         const long long G = gridDim.x;
         const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
         const int n_inner = p.d0.n_inner;
+        int o = (int)(w0 / n_inner), in = (int)(w0 % n_inner);
         for (long long w = w0; w < w1 && ok; ++w) {
-          const int o = (int)(w / n_inner), in = (int)(w % n_inner);
           const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
                             ((w + 1 == w1 || in + 1 == n_inner) ? META_LAST : 0);
           ok = push(0, o, in, flags, (int)(i - p.first_cta[o]));
+          if (++in == n_inner) {
+            in = 0;
+            ++o;
+          }
         }
       } else {
         while (ok) {
@@ -270,12 +275,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     if (lane == 0) {
       constexpr uint32_t idesc_ph = idesc_f16(64);
       bool ok = true;
-      long long gs = 0;
+      Ring<NBUF> rb;
+      Ring<NSLOT> rs;
+      int warm = 0;  // stages issued, counted up to NSLOT (a slot's first use has no wait)
       int prun = 0, prs = 0;
-      for (long long it = 0; ok; ++it) {
-        const int buf = (int)(it % NBUF);
-        if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2,
-                       LIM)) {
+      for (; ok; rb.next()) {
+        const int buf = rb.idx;
+        if (!mbar_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 2, LIM)) {
           ok = false;
           break;
         }
@@ -294,11 +300,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
         // 32-byte step inside a 128-byte row adds 2 to the start-address field
         const uint64_t da = desc_sw128(smem_u32(sPr + prs * LY::PR_BYTES));
         const uint64_t db0 = desc_sw128(smem_u32(sPc + buf * LY::PC_BYTES));
-        for (int st = 0; st < 2; ++st, ++gs) {
-          const int slot = (int)(gs % NSLOT);
+        for (int st = 0; st < 2; ++st, rs.next()) {
+          const int slot = rs.idx;
           // the slot is free once the contraction MMAs of its previous stage have completed
-          if (gs >= NSLOT && !mbar_wait(smem_u32(&tempty[slot]), (uint32_t)(gs / NSLOT - 1) & 1u,
-                                        abort_flag, p.err, 13, LIM)) {
+          if (warm < NSLOT) {
+            ++warm;
+          } else if (!mbar_wait(smem_u32(&tempty[slot]), rs.phase ^ 1u, abort_flag, p.err, 13,
+                                LIM)) {
             ok = false;
             break;
           }
@@ -342,21 +350,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       constexpr uint32_t idesc = idesc_f16(NM);
       const uint32_t dst = role == 0 ? D1 : D2;
       bool ok = true;
-      long long it = 0, gstage = 0;
-      int seg = 0, run_pos = 0;
-      for (; ok; ++it) {
-        const int buf = (int)(it % NBUF);
-        if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 15,
-                       LIM)) {
+      Ring<NBUF> rb;
+      Ring<NSLOT> rs;
+      int seg = 0, seg_pos = 0;  // segments issued; position of the block in its segment
+      for (; ok; rb.next()) {
+        const int buf = rb.idx;
+        if (!mbar_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 15, LIM)) {
           ok = false;
           break;
         }
         const int flags = sMeta[buf].flags;
         if (flags & META_END) break;
-        if (flags & META_FIRST) run_pos = 0;
-        const bool seg_first = (flags & META_FIRST) || (run_pos % F == 0);
-        const bool seg_last = (flags & META_LAST) || ((run_pos + 1) % F == 0);
-        ++run_pos;
+        if (flags & META_FIRST) seg_pos = 0;
+        const bool seg_first = seg_pos == 0;
+        const bool seg_last = (flags & META_LAST) || seg_pos + 1 == F;
+        seg_pos = seg_last ? 0 : seg_pos + 1;
         if (seg_first && seg > 0) {
           if (!mbar_wait(smem_u32(aempty), (uint32_t)(seg - 1) & 1u, abort_flag, p.err, 3, LIM)) {
             ok = false;
@@ -365,10 +373,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
           tc_fence_after();
         }
         const uint32_t sbuf = smem_u32(sB + buf * LY::B_BYTES);
-        for (int st = 0; st < 2; ++st, ++gstage) {
-          const int slot = (int)(gstage % NSLOT);
-          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / NSLOT) & 1u, abort_flag,
-                         p.err, 4, LIM)) {
+        for (int st = 0; st < 2; ++st, rs.next()) {
+          const int slot = rs.idx;
+          if (!mbar_wait(smem_u32(&tfull[slot]), rs.phase, abort_flag, p.err, 4, LIM)) {
             ok = false;
             break;
           }
@@ -427,8 +434,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
         pending = -1;
       }
     };
-    long long it = 0, gstage = 0;
-    int seg = 0, run = 0, run_pos = 0;
+    Ring<NBUF> rb;
+    Ring<NSLOT> rs;
+    int seg = 0, run = 0, seg_pos = 0;  // segments, runs; position of the block in its segment
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
@@ -510,17 +518,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       ++run;
       return true;
     };
-    for (;; ++it) {
-      const int buf = (int)(it % NBUF);
-      if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5, LIM)) {
+    for (;; rb.next()) {
+      const int buf = rb.idx;
+      if (!warp_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 5, LIM)) {
         ok = false;
         break;
       }
       const Meta m = sMeta[buf];
       if (m.flags & META_END) break;
-      if (m.flags & META_FIRST) run_pos = 0;
-      const bool seg_last = (m.flags & META_LAST) || ((run_pos + 1) % F == 0);
-      ++run_pos;
+      if (m.flags & META_FIRST) seg_pos = 0;
+      const bool seg_last = (m.flags & META_LAST) || seg_pos + 1 == F;
+      seg_pos = seg_last ? 0 : seg_pos + 1;
       const InstDesc& dm = desc(m.inst);
       const float2 us2 = make_float2(dm.ph_unscale, dm.ph_unscale);
       const float* anc = sAnc + buf * 128;
@@ -532,10 +540,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       const uint4* ptile =
           STORED ? dm.stored + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
                  : nullptr;
-      for (int st = 0; st < 2; ++st, ++gstage) {
-        const int slot = (int)(gstage % NSLOT);
-        if (!warp_wait(smem_u32(&pfull[slot]), (uint32_t)(gstage / NSLOT) & 1u, abort_flag, p.err,
-                       6, LIM)) {
+      for (int st = 0; st < 2; ++st, rs.next()) {
+        const int slot = rs.idx;
+        if (!warp_wait(smem_u32(&pfull[slot]), rs.phase, abort_flag, p.err, 6, LIM)) {
           ok = false;
           break;
         }
