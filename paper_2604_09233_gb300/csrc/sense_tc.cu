@@ -157,15 +157,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     // ------------------------------------------------------------------ loader
     if (lane == 0) {
       const uint32_t col_bytes = 128u * RT * 4u;
-      long long it = 0;
+      long long it = 0;   // blocks pushed
+      Ring<NBUF> rb;      // ring position of block it
       bool ok = true;
       // claim the next stage buffer and publish its metadata; with data, also issue the
       // stage's bulk copies (the full barrier completes when they land)
       auto push = [&](int b, int o, int in, int flags, int slot) -> bool {
-        const int buf = (int)(it % NBUF);
-        const uint32_t use = (uint32_t)(it / NBUF);
-        if (use > 0 &&
-            !mbar_wait(smem_u32(&empty[buf]), (use - 1) & 1u, abort_flag, p.err, 1, LIM))
+        const int buf = rb.idx;
+        if (it >= NBUF &&
+            !mbar_wait(smem_u32(&empty[buf]), rb.phase ^ 1u, abort_flag, p.err, 1, LIM))
           return false;
         Meta m;
         m.inst = b; m.o = o; m.in = in; m.flags = flags; m.slot = slot;
@@ -192,17 +192,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           }
         }
         ++it;
+        rb.next();
         return true;
       };
       if (!queue) {
         const long long G = gridDim.x;
         const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
         const int n_inner = p.d0.n_inner;
+        int o = (int)(w0 / n_inner), in = (int)(w0 % n_inner);
         for (long long w = w0; w < w1 && ok; ++w) {
-          const int o = (int)(w / n_inner), in = (int)(w % n_inner);
           const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
                             ((w + 1 == w1 || in + 1 == n_inner) ? META_LAST : 0);
           ok = push(0, o, in, flags, (int)(i - p.first_cta[o]));
+          if (++in == n_inner) {
+            in = 0;
+            ++o;
+          }
         }
       } else {
         while (ok) {
@@ -235,21 +240,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16(2 * CP);
-      long long it = 0, gstage = 0;
-      int seg = 0, run_pos = 0;
+      Ring<NBUF> rb;
+      Ring<SM::NSLOT> rs;
+      int seg = 0, seg_pos = 0;  // segments issued; position of the block in its segment
       bool ok = true;
-      for (;; ++it) {
-        const int buf = (int)(it % NBUF);
-        if (!mbar_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 2, LIM)) {
+      for (;; rb.next()) {
+        const int buf = rb.idx;
+        if (!mbar_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 2, LIM)) {
           ok = false;
           break;
         }
         const int flags = sMeta[buf].flags;
         if (flags & META_END) break;
-        if (flags & META_FIRST) run_pos = 0;
-        const bool seg_first = (flags & META_FIRST) || (run_pos % F == 0);
-        const bool seg_last = (flags & META_LAST) || ((run_pos + 1) % F == 0);
-        ++run_pos;
+        if (flags & META_FIRST) seg_pos = 0;
+        const bool seg_first = seg_pos == 0;
+        const bool seg_last = (flags & META_LAST) || seg_pos + 1 == F;
+        seg_pos = seg_last ? 0 : seg_pos + 1;
         if (seg_first && seg > 0) {
           if (!mbar_wait(smem_u32(aempty), (uint32_t)(seg - 1) & 1u, abort_flag, p.err, 3, LIM)) {
             ok = false;
@@ -258,10 +264,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
           tc_fence_after();
         }
         const uint32_t sbuf = smem_u32(sB + buf * SM::B_BYTES);
-        for (int st = 0; st < 2; ++st, ++gstage) {
-          const int slot = (int)(gstage % SM::NSLOT);
-          if (!mbar_wait(smem_u32(&tfull[slot]), (uint32_t)(gstage / SM::NSLOT) & 1u, abort_flag,
-                         p.err, 4, LIM)) {
+        for (int st = 0; st < 2; ++st, rs.next()) {
+          const int slot = rs.idx;
+          if (!mbar_wait(smem_u32(&tfull[slot]), rs.phase, abort_flag, p.err, 4, LIM)) {
             ok = false;
             break;
           }
@@ -337,8 +342,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         pending = -1;
       }
     };
-    long long it = 0, gstage = 0;
-    int seg = 0, run = 0, run_pos = 0;
+    Ring<NBUF> rb;
+    Ring<SM::NSLOT> rs;
+    int warm = 0;  // stages generated, counted up to NSLOT (a slot's first use has no wait)
+    int seg = 0, run = 0, seg_pos = 0;  // segments, runs; position of the block in its segment
     bool ok = true;
     int cur_b = -1, cur_o = -1;
 #pragma unroll
@@ -419,17 +426,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       ++run;
       return true;
     };
-    for (;; ++it) {
-      const int buf = (int)(it % NBUF);
-      if (!warp_wait(smem_u32(&full[buf]), (uint32_t)(it / NBUF) & 1u, abort_flag, p.err, 5, LIM)) {
+    for (;; rb.next()) {
+      const int buf = rb.idx;
+      if (!warp_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 5, LIM)) {
         ok = false;
         break;
       }
       const Meta m = sMeta[buf];
       if (m.flags & META_END) break;
-      if (m.flags & META_FIRST) run_pos = 0;
-      const bool seg_last = (m.flags & META_LAST) || ((run_pos + 1) % F == 0);
-      ++run_pos;
+      if (m.flags & META_FIRST) seg_pos = 0;
+      const bool seg_last = (m.flags & META_LAST) || seg_pos + 1 == F;
+      seg_pos = seg_last ? 0 : seg_pos + 1;
       if (!STORED && (m.o != cur_o || m.inst != cur_b)) {
         cur_o = m.o;
         cur_b = m.inst;
@@ -446,11 +453,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
       const float* anc = sAnc + buf * 128;
       const float rb = sRowAnc[buf * 128 + row];
       const float2 rb2 = make_float2(rb, rb);
-      for (int st = 0; st < 2; ++st, ++gstage) {
-        const int slot = (int)(gstage % SM::NSLOT);
-        if (gstage >= SM::NSLOT &&
-            !warp_wait(smem_u32(&tempty[slot]), (uint32_t)(gstage / SM::NSLOT - 1) & 1u,
-                       abort_flag, p.err, 6, LIM)) {
+      for (int st = 0; st < 2; ++st, rs.next()) {
+        const int slot = rs.idx;
+        if (warm < SM::NSLOT) {
+          ++warm;
+        } else if (!warp_wait(smem_u32(&tempty[slot]), rs.phase ^ 1u, abort_flag, p.err, 6,
+                              LIM)) {
           ok = false;
           break;
         }
