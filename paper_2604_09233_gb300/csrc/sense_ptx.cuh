@@ -74,7 +74,33 @@ struct Ring {
       phase ^= 1u;
     }
   }
+  // the position after this one
+  __device__ __forceinline__ Ring peek() const {
+    Ring r = *this;
+    r.next();
+    return r;
+  }
 };
+
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Warp-uniform non-blocking test (lane 0 tests, every lane gets the outcome).
+__device__ __forceinline__ bool warp_test(uint32_t bar, uint32_t parity) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_test(bar, parity) ? 1 : 0;
+  return __any_sync(0xffffffffu, ok) != 0;
+}
 
 // Warp-uniform bounded wait: lane 0 polls, every lane gets the outcome and the warp is
 // converged on return (required before .sync.aligned tcgen05 instructions).

@@ -438,6 +438,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     Ring<NSLOT> rs;
     int seg = 0, run = 0, seg_pos = 0;  // segments, runs; position of the block in its segment
     bool ok = true;
+    // the next block's data / the next stage's phases, found ready by a test made during the
+    // previous stage's arithmetic (so that the test's latency is hidden behind it)
+    bool next_full = false, next_pfull = false;
 #pragma unroll
     for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
     bool drain_due = false, d_out = false;
@@ -520,10 +523,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     };
     for (;; rb.next()) {
       const int buf = rb.idx;
-      if (!warp_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 5, LIM)) {
+      if (!next_full && !warp_wait(smem_u32(&full[buf]), rb.phase, abort_flag, p.err, 5, LIM)) {
         ok = false;
         break;
       }
+      next_full = false;
       const Meta m = sMeta[buf];
       if (m.flags & META_END) break;
       if (m.flags & META_FIRST) seg_pos = 0;
@@ -532,8 +536,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       const InstDesc& dm = desc(m.inst);
       const float2 us2 = make_float2(dm.ph_unscale, dm.ph_unscale);
       const float* anc = sAnc + buf * 128;
-      const float rb = sRowAnc[buf * 128 + row];
-      const float2 rb2 = make_float2(rb, rb);
+      const float ranc = sRowAnc[buf * 128 + row];
+      const float2 rb2 = make_float2(ranc, ranc);
       uint4* emit = p.emit ? p.emit + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
                            : nullptr;
       // stored tiles of this pair: 16 chunks (stage, warpgroup, half) of [4][128] uint4
@@ -542,10 +546,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
                  : nullptr;
       for (int st = 0; st < 2; ++st, rs.next()) {
         const int slot = rs.idx;
-        if (!warp_wait(smem_u32(&pfull[slot]), rs.phase, abort_flag, p.err, 6, LIM)) {
+        if (!next_pfull && !warp_wait(smem_u32(&pfull[slot]), rs.phase, abort_flag, p.err, 6, LIM)) {
           ok = false;
           break;
         }
+        next_pfull = false;
         tc_fence_after();
         const uint32_t acol = tmem + lane_base + LY::ACOL0 + slot * LY::SLOT_COLS + g * 8;
         if (STORED) {
@@ -591,6 +596,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
         tmem_ld8x2(acol, acol + 32, dv);
 #pragma unroll
         for (int jh = 0; jh < 2; ++jh) {
+          if (jh == 1) {
+            // what the next stage waits for: its phases (same block) or the next block
+            if (st == 0) {
+              const Ring<NSLOT> nr = rs.peek();
+              next_pfull = warp_test(smem_u32(&pfull[nr.idx]), nr.phase);
+            } else {
+              const Ring<NBUF> nb = rb.peek();
+              next_full = warp_test(smem_u32(&full[nb.idx]), nb.phase);
+            }
+          }
           uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
           const int v0 = st * 64 + g * 16 + 8 * jh;
           const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
