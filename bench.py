@@ -48,6 +48,8 @@ def _parse():
                     help="skip the (untimed) differentiation measurements")
     ap.add_argument("--no-stored", action="store_true",
                     help="skip the (untimed) stored-P comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the (untimed) 3D and batch workloads of the default line")
     ap.add_argument("--stored", action="store_true",
                     help="--op-only: stream stored phase tiles instead of generating them")
     ap.add_argument("--op-only", action="store_true",
@@ -310,6 +312,32 @@ def _kernel_traffic(workload, prec_name, kernel):
     return rec.get(kernel)
 
 
+GOLDEN_CG = {"2d_256x256_32coil_35750samp_sh3": os.path.join(ROOT, "tests", "golden",
+                                                               "cg_target_256.txt")}
+
+
+def golden_cg(workload):
+    """FP64 oracle CG iterates stored for a workload (written by tests/golden/make_cg_target_256.py
+    from the oracle alone): {"voxels": int array, "iterates": {n: complex array}} or None."""
+    path = GOLDEN_CG.get(workload)
+    if path is None or not os.path.exists(path):
+        return None
+    cols = None
+    rows = []
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("# columns:"):
+                cols = ln.split(":", 1)[1].split()
+            elif ln.strip() and not ln.startswith("#"):
+                rows.append([float(v) for v in ln.split()])
+    a = np.asarray(rows)
+    its = sorted({int(c.split("_")[1]) for c in cols[1:]})
+    out = {"voxels": a[:, 0].astype(np.int64), "iterates": {}}
+    for n in its:
+        out["iterates"][n] = a[:, cols.index(f"re_{n}")] + 1j * a[:, cols.index(f"im_{n}")]
+    return out
+
+
 def max_over_ranks(total_ms, world, device=None):
     """The largest of the ranks' timed totals, returned on every rank (the job takes as long
     as its slowest replica)."""
@@ -408,6 +436,33 @@ def run_ours(args):
     native.sense_cg_solve(plan.handle, s, x_ref, n_it, prec=native.SENSE_PREC_FP32, history=False)
     torch.cuda.synchronize()
     err_vs_fp32 = (torch.linalg.norm(x_tc - x_ref) / torch.linalg.norm(x_ref)).item()
+
+    # ---------------------------------------------------------------- vs the FP64 oracle (untimed)
+    # relative L2 over the stored voxels of the CG iterates after n iterations, against the
+    # FP64 oracle's CG (the CG loop of Alg. 1) on the same phantom and noise
+    vs_oracle = None
+    gold = golden_cg(wl.name)
+    if gold is not None:
+        vox = torch.from_numpy(gold["voxels"]).to(dev)
+        vs_oracle = {"source": "tests/golden/cg_target_256.txt: FP64 oracle CG iterates on "
+                               f"{len(gold['voxels'])} voxels (every 64th)",
+                     "sigma": "E m by the FP32 path + the same noise; the oracle's own FP64 "
+                              "E m differs by ~1e-7 relative, which CG amplifies with the "
+                              "iteration count (FP64 CG moves by >1e-3 under such a "
+                              "perturbation within 15-20 iterations)"}
+        for name, pv in ((prec_name, prec), ("fp32", native.SENSE_PREC_FP32)):
+            errs = {}
+            for n_g, ref in gold["iterates"].items():
+                if n_g == n_it and pv == prec:
+                    xg = x_tc
+                elif n_g == n_it and pv == native.SENSE_PREC_FP32:
+                    xg = x_ref
+                else:
+                    xg = torch.empty_like(x)
+                    native.sense_cg_solve(plan.handle, s, xg, n_g, prec=pv, history=False)
+                got = xg[vox].cpu().numpy().astype(np.complex128)
+                errs[str(n_g)] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            vs_oracle[name] = {"rel_l2_by_iterations": errs}
 
     # ---------------------------------------------------------------- e2e (host buffers)
     s_host = torch.empty((wl.K, wl.C), dtype=torch.complex64).pin_memory()
@@ -551,6 +606,27 @@ def run_ours(args):
             maps["eq3_b0"][pc] = {"ms": ms, "iterations": inf["iters"],
                                   "rel_residual": inf["rel_residual"]}
 
+    # ---------------------------------------------------------------- 3D and batch (untimed)
+    # the other named workloads, measured on the same GPU in the same run: the 3D stack of
+    # spirals (applies/s of E^H E per precision and a few CG iterations against the FP32
+    # path) and both 64-instance batches (one batched solve each against the same instances
+    # solved one after another)
+    extra3d, batches = None, None
+    if not args.no_extra and args.workload == "target_256" and world == 1:
+        extra3d = measure_3d(dev, prec_name)
+        batches = {}
+        for bw in BATCH_WORKLOADS:
+            try:
+                r = batch_measure(bw, prec_name, 1, 1, dev, full=False)
+                batches[bw] = {k: r[k] for k in ("value", "ms_per_step", "speedup_vs_sequential",
+                                                 "sequential_single_problem_ms",
+                                                 "voxel_sample_coil_gops", "roofline",
+                                                 "iterations_per_instance")}
+                batches[bw]["unit"] = UNIT + " summed over instances"
+                batches[bw]["config"] = r["config"]
+            except native.SenseError as e:
+                batches[bw] = {"unavailable": str(e)}
+
     # ---------------------------------------------------------------- roofline
     # dominant kernel: the tensor-core pass (E or E^H) with the larger share of event time
     peaks, peak_kind = _peaks()
@@ -601,6 +677,7 @@ def run_ours(args):
         "applies_per_s_by_precision": rates,
         "speedup_vs_fp32_path": rates["tc_split"] / rates["fp32"],
         "cg_rel_err_vs_fp32_path": err_vs_fp32,
+        "cg_vs_fp64_oracle": vs_oracle,
         "roofline": roof,
         "roofline_other": tensor if roof is sfu else sfu,
         "roofline_issue": issue,
@@ -618,6 +695,10 @@ def run_ours(args):
         line["stored_p"] = stored
     if maps is not None:
         line["map_smoothing"] = maps
+    if extra3d is not None:
+        line["stack_3d"] = extra3d
+    if batches is not None:
+        line["batch"] = batches
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_apply_rate(wl)
         cb.pop("seconds")
@@ -639,26 +720,74 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def measure_3d(dev, prec_name, cg_iters=5):
+    """The 3D workload (96x96x48, 32 coils, 48 x 1300 samples, 2nd-order terms), untimed
+    within the benchmark step: E^H E applies/s per precision (three applies each, events on
+    the launching stream) and a short CG in the benchmark precision against the FP32 path."""
+    import torch
+    from paper_2604_09233_gb300 import native, synthetic
+    wl = synthetic.stack_3d()
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    plan = native.Plan(wl.Kmat, wl.Rmat, wl.S, wl.j)
+    t_plan = time.perf_counter() - t0
+    try:
+        m = torch.from_numpy(wl.m_true.astype(np.complex64)).to(dev)
+        s = plan.encode(m) + torch.from_numpy(wl.noise.astype(np.complex64)).to(dev)
+        q = torch.empty_like(m)
+
+        def rate(p, reps):
+            native.sense_normal_op(plan.handle, p, m, q)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(reps):
+                native.sense_normal_op(plan.handle, p, m, q)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return reps / (ev[0].elapsed_time(ev[1]) / 1e3)
+
+        rates = {"tc_split": rate(native.SENSE_PREC_TC_SPLIT, 3),
+                 "tc_fp16": rate(native.SENSE_PREC_TC_FP16, 3),
+                 "fp32": rate(native.SENSE_PREC_FP32, 2)}
+        prec = native.PRECISIONS[prec_name]
+        x = torch.empty_like(m)
+        xr = torch.empty_like(m)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        native.sense_cg_solve(plan.handle, s, x, cg_iters, prec=prec, history=False)
+        ev[1].record(stream)
+        native.sense_cg_solve(plan.handle, s, xr, cg_iters, prec=native.SENSE_PREC_FP32,
+                              history=False)
+        torch.cuda.synchronize()
+        err = (torch.linalg.norm(x - xr) / torch.linalg.norm(xr)).item()
+        info = plan.info
+        return {"workload": wl.name, "L": wl.L, "K": wl.K, "coils": wl.C,
+                "applies_per_s_by_precision": rates,
+                "speedup_vs_fp32_path": rates["tc_split"] / rates["fp32"],
+                "voxel_sample_coil_gops_split": rates["tc_split"] * 2.0 * wl.L * wl.K * wl.C / 1e9,
+                "cg_iters": cg_iters, "cg_ms": ev[0].elapsed_time(ev[1]),
+                "cg_rel_err_vs_fp32_path": err, "plan_create_s": t_plan,
+                "padded": [info["L_padded"], info["K_padded"], info["C_padded"]]}
+    finally:
+        plan.close()
+
+
 BATCH_METRIC = "E^H E applies/s summed over instances (batched CG, uneven instances)"
 
 
 BATCH_WORKLOADS = {"batch_64": "batch_64_2d_uneven", "batch_small_64": "batch_64_2d_small"}
 
 
-def run_batch(args):
+def batch_measure(workload, prec_name, steps, warmup, dev, full=True):
     """64 independent uneven 2D instances solved by one batched CG (per-instance stop at
     relative residual 1e-3, at most 50 iterations). A step is one sense_batch_cg_solve.
     batch_64: matrices {64..256}^2 (most instances fill the GPU alone); batch_small_64:
-    matrices {64, 96}^2 with 4096-8192 samples, where one instance underfills 152 SMs."""
+    matrices {64, 96}^2 with 4096-8192 samples, where one instance underfills 152 SMs.
+    Returns the measured fields; full=False skips the clock sampling and the e2e leg."""
     import torch
     from paper_2604_09233_gb300 import native, synthetic
-    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
-        return
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
-    prec_name = "tc_split" if args.prec == "auto" else args.prec
     prec = native.PRECISIONS[prec_name]
-    wls = getattr(synthetic, args.workload)()
+    wls = getattr(synthetic, workload)()
     t0 = time.perf_counter()
     batch = native.Batch([(w.Kmat, w.Rmat, w.S, w.j) for w in wls])
     t_create = time.perf_counter() - t0
@@ -678,12 +807,15 @@ def run_batch(args):
     def solve():
         return native.sense_batch_cg_solve(batch.handle, sig, xs, n_it, prec=prec, rel_tol=tol)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(1, warmup)):
         infos = solve()
     torch.cuda.synchronize()
     times = []
-    with ClockSampler(dev.index) as clk:
-        for i in range(args.steps):
+    clk = ClockSampler(dev.index) if full else None
+    if clk is not None:
+        clk.__enter__()
+    try:
+        for i in range(steps):
             flush.fill_(float(i))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -691,10 +823,13 @@ def run_batch(args):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+    finally:
+        if clk is not None:
+            clk.__exit__(None, None, None)
     total_ms = float(np.sum(times))
     iters = [inf["iters"] for inf in infos]
     applies = float(sum(iters))
-    value = applies * args.steps / (total_ms / 1e3)
+    value = applies * steps / (total_ms / 1e3)
     vsc = sum(it * 2.0 * w.L * w.K * w.C for it, w in zip(iters, wls))
 
     # the same instances solved one after another through the single-problem API
@@ -707,23 +842,6 @@ def run_batch(args):
     torch.cuda.synchronize()
     seq_ms = ev[0].elapsed_time(ev[1])
 
-    # e2e: pinned host data in, solve, images out
-    s_host = [s.cpu().pin_memory() for s in sig]
-    x_host = [torch.empty(w.L, dtype=torch.complex64).pin_memory() for w in wls]
-    e2e_t = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for d, h in zip(sig, s_host):
-            d.copy_(h, non_blocking=True)
-        solve()
-        for h, d in zip(x_host, xs):
-            h.copy_(d, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t1)
-    e2e_value = applies * len(e2e_t) / float(np.sum(e2e_t))
-
     # roofline of the batched E^H E (both persistent passes and the per-instance kernels),
     # timed by the autotuner: phase pairs generated per apply / time
     pairs = 0.0
@@ -733,37 +851,67 @@ def run_batch(args):
     sincos_peak = native.sense_diag_sincos_rate(300.0)
     achieved = pairs / (tune["ms"] / 1e3)
     n = len(wls)
-    clocks = clk.summary()
-    line = {
-        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOADS[args.workload], "instances": n,
+    out = {
+        "value": value, "ms_per_step": total_ms / steps,
+        "config": {"workload": BATCH_WORKLOADS[workload], "instances": n,
                    "matrices": sorted({w.shape[0] for w in wls}),
                    "coils": sorted({w.C for w in wls}),
                    "samples": [min(w.K for w in wls), max(w.K for w in wls)],
                    "max_iter": n_it, "rel_tol": tol, "precision": prec_name,
                    "l2": "flushed between steps (256 MiB write)"},
-        "voxel_sample_coil_gops": vsc * args.steps / (total_ms / 1e3) / 1e9,
+        "voxel_sample_coil_gops": vsc * steps / (total_ms / 1e3) / 1e9,
         "iterations_per_instance": iters,
         "sequential_single_problem_ms": seq_ms,
-        "speedup_vs_sequential": seq_ms / (total_ms / args.steps),
+        "speedup_vs_sequential": seq_ms / (total_ms / steps),
         "autotune": tune,
         "batch_create_s": t_create,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": sincos_peak / 1e9,
                      "unit": "Gsincos/s", "frac": achieved / sincos_peak, "traffic": None,
                      "kernel": "batched E^H E (two persistent passes + per-instance kernels)",
                      "peak_source": "measured on this GPU by sense_diag_sincos_rate"},
-        "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(sum(w.K * w.C * 8 for w in wls)),
-                "d2h_bytes_per_step": int(sum(w.L * 8 for w in wls))},
         # per step: 8 kernels per instance outside the loop (data layout, ||s||, E^H s: 4,
         # CG init, result) + per iteration 2 batched passes + 8 per instance
         "gpu_launches": 8 * n + n_it * (2 + 8 * n),
     }
-    print(json.dumps(line), flush=True)
+    if full:
+        out["clocks"] = clk.summary()
+        # e2e: pinned host data in, solve, images out
+        s_host = [sv.cpu().pin_memory() for sv in sig]
+        x_host = [torch.empty(w.L, dtype=torch.complex64).pin_memory() for w in wls]
+        e2e_t = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for d, h in zip(sig, s_host):
+                d.copy_(h, non_blocking=True)
+            solve()
+            for h, d in zip(x_host, xs):
+                h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t1)
+        out["e2e"] = {"value": applies * len(e2e_t) / float(np.sum(e2e_t)), "unit": UNIT,
+                      "h2d_bytes_per_step": int(sum(w.K * w.C * 8 for w in wls)),
+                      "d2h_bytes_per_step": int(sum(w.L * 8 for w in wls))}
     batch.close()
+    return out
+
+
+def run_batch(args):
+    """The batch workloads as the benchmark's own line (see batch_measure)."""
+    import torch
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prec_name = "tc_split" if args.prec == "auto" else args.prec
+    res = batch_measure(args.workload, prec_name, args.steps, max(3, args.warmup), dev)
+    line = {"metric": BATCH_METRIC, "value": res.pop("value"), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+            "data": "synthetic", "config": res.pop("config")}
+    line.update(res)
+    print(json.dumps(line), flush=True)
 
 
 def main():

@@ -407,7 +407,10 @@ extern "C" int sense_batch_cg_solve(sense_batch B, const float* const* s, float*
       if (rc != SENSE_OK) return rc;
       B->graph_prec = opts->prec;
     }
-    for (int it = 1; it < N; ++it) SENSE_CUDA_TRY(cudaGraphLaunch(B->gexec, st));
+    for (int it = 1; it < N; ++it) {
+      NvtxRange nvtx("sense batch CG iteration (graph)");
+      SENSE_CUDA_TRY(cudaGraphLaunch(B->gexec, st));
+    }
   }
   for (int b = 0; b < n; ++b)
     BTRY(scatter_image(B->plans[b], B->plans[b]->vx, (float2*)x[b], opts->apply_j != 0, st));

@@ -359,6 +359,7 @@ int check_prec(int prec) {
 int apply_normal_internal(sense_plan_s* P, int prec, const float2* p, float2* q,
                           const double* stop, cudaStream_t st) {
   int rc;
+  NvtxRange nvtx("sense E^H E");
   if (prec != SENSE_PREC_FP32) {
     if ((rc = tc_encode(P, prec, p, P->Y, nullptr, true, stop, st)) != SENSE_OK) return rc;
     return tc_adjoint(P, prec, P->Y, q, true, stop, st);
@@ -622,6 +623,7 @@ int cg_run(sense_plan_s* P, const float* s, float* x, const sense_cg_opts* opts,
   if (iterates && !x0) SENSE_CUDA_TRY(cudaMemsetAsync(iterates, 0, (size_t)P->L * 8, st));
   if (iterates && x0 && opts->apply_j) TRY(scatter_image(P, P->vx, iterates, true, st));
   for (int n = 0; n < N; ++n) {
+    NvtxRange nvtx("sense CG iteration");
     if (ckpt_every > 0 && n % ckpt_every == 0) TRY(ckpt_save(P, ckpt, n / ckpt_every, st));
     // q = E^H E p
     TRY(apply_normal_internal(P, opts->prec, P->vp, P->vq, stop, st));

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -10,6 +11,16 @@
 #include "../../include/sense.h"
 
 namespace sense {
+
+// Named NVTX range for the host-side span of a scope (plan creation, a CG solve and each of
+// its iterations, an E^H E apply, a tensor-core pass); visible to nsys / ncu --nvtx, a few
+// tens of nanoseconds per range otherwise.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Anchor block size: samples are grouped in blocks of TILE consecutive samples, voxels
 // in spatially compact blocks of TILE (k-d order). Every kernel tile lies inside one

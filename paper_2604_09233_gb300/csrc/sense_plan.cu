@@ -475,6 +475,7 @@ extern "C" int sense_plan_create(const sense_problem* prob, sense_plan* out) {
 namespace sense {
 
 int plan_create(const sense_problem* prob, int min_cp, int min_rt, sense_plan_s** out) {
+  NvtxRange nvtx("sense plan create");
   if (!prob || !out) return set_error(SENSE_EINVAL, "null problem or output pointer");
   *out = nullptr;
   if (prob->L < 1 || prob->K < 1 || prob->C < 1 || prob->P1 < 1)

@@ -969,6 +969,7 @@ int tc_make_image(sense_plan_s* P, int npart, const float2* src, const float2* p
 
 static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, const float* bscale,
                     float2* out, const double* stop, cudaStream_t st) {
+  NvtxRange nvtx(mode == tc::ENC ? "sense tensor-core E pass" : "sense tensor-core E^H pass");
   tc::Params prm = {};
   const bool enc = mode == tc::ENC;
   tc::InstDesc& d = prm.d0;

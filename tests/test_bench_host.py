@@ -49,3 +49,23 @@ def test_traffic_lookup_is_specific_to_the_captured_case():
         assert bench._kernel_traffic(wl, prec, "tc_adjoint_pass") == rec["tc_adjoint_pass"]
         assert bench._kernel_traffic(wl, "tc_fp16", "tc_adjoint_pass") is None
     assert bench._kernel_traffic("another_workload", "tc_split", "tc_adjoint_pass") is None
+
+
+def test_golden_cg_reader_matches_the_stored_text():
+    """The bench's reader of the stored FP64 CG iterates returns every stored voxel and
+    iteration count, with values equal to the text and norms equal to the header's norms
+    scaled by the sampled fraction (every 64th voxel of a smooth image: same order of size)."""
+    import numpy as np
+    g = bench.golden_cg("2d_256x256_32coil_35750samp_sh3")
+    assert g is not None
+    assert list(g["voxels"][:3]) == [0, 64, 128] and len(g["voxels"]) == 65536 // 64
+    assert sorted(g["iterates"]) == [5, 10, 40]
+    path = bench.GOLDEN_CG["2d_256x256_32coil_35750samp_sh3"]
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert g["iterates"][40][7] == complex(float(rows[7][5]), float(rows[7][6]))
+    head = [ln for ln in open(path) if ln.startswith("# norms")][0]
+    full = {int(t.split(":")[0]): float(t.split(":")[1]) for t in head.split(":", 1)[1].split()}
+    for n, v in g["iterates"].items():
+        sampled = np.linalg.norm(v) * np.sqrt(64.0)
+        assert 0.5 < sampled / full[n] < 2.0
+    assert bench.golden_cg("another_workload") is None
