@@ -597,14 +597,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
 #pragma unroll
         for (int jh = 0; jh < 2; ++jh) {
           if (jh == 1) {
-            // what the next stage waits for: its phases (same block) or the next block
-            if (st == 0) {
-              const Ring<NSLOT> nr = rs.peek();
-              next_pfull = warp_test(smem_u32(&pfull[nr.idx]), nr.phase);
-            } else {
+            // what the next stage waits for: at a block's end the next block's data, and its
+            // phases (each barrier observed directly, for the ordering of what it guards)
+            const Ring<NSLOT> nr = rs.peek();
+            if (st == 1) {
               const Ring<NBUF> nb = rb.peek();
               next_full = warp_test(smem_u32(&full[nb.idx]), nb.phase);
             }
+            next_pfull = (st == 0 || next_full) && warp_test(smem_u32(&pfull[nr.idx]), nr.phase);
           }
           uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
           const int v0 = st * 64 + g * 16 + 8 * jh;
