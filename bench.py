@@ -257,27 +257,19 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
-# DRAM bytes per launch of the tensor-core passes (dram__bytes_read.sum + dram__bytes_write.sum
-# from one ncu capture, profiles/tc_pass_2d256_32coil_sh3.md), keyed by the SHA-256 of the
-# pass-kernel source they were taken on (pass_kernel_source_hash); any other source reports null.
+# DRAM bytes per launch of the tensor-core passes (dram__bytes_read.sum + dram__bytes_write.sum)
+# and warp instructions executed per launch (smsp__inst_executed.sum), from one ncu capture of
+# `python bench.py --op-only --steps 1 --warmup 2` (profiles/tcp_pass_2d256_32coil_sh3.md), keyed
+# by the SHA-256 of the pass-kernel source they were taken on (pass_kernel_source_hash); any other
+# source reports null.
 KERNEL_TRAFFIC = {
-    "9d6b40d3d0513d3e2a084353fece0b2b71af22771ff8bfab8d40f4eadb118811": {
+    "107444c196ea2e131360d5f0358822b824876fd08b6a37e4b5457b5076af4bd8": {
         "2d_256x256_32coil_35750samp_sh3": {
             "precision": "tc_split",
-            "tc_encode_pass": 168462080 + 9367040,
-            "tc_adjoint_pass": 182305536 + 378112,
-            "stored_tc_encode_pass": 19522951680 + 12660992,
-            "stored_tc_adjoint_pass": 19492078592 + 681216,
-            # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
-            "inst_tc_encode_pass": 2459430132,
-            "inst_tc_adjoint_pass": 2519748336,
-        },
-        "3d_96x96x48_32coil_62400samp_sh2": {
-            "precision": "tc_split",
-            "tc_encode_pass": 11170881536 + 21115392,
-            "tc_adjoint_pass": 1890571520 + 4946432,
-            "inst_tc_encode_pass": 28915454995,
-            "inst_tc_adjoint_pass": 29616864412,
+            "tc_encode_pass": 174737920 + 9260800,
+            "tc_adjoint_pass": 190799872 + 444672,
+            "inst_tc_encode_pass": 1485124734,
+            "inst_tc_adjoint_pass": 1511146539,
         },
     },
 }
