@@ -367,13 +367,21 @@ int sense_plan_store_p(sense_plan plan, int32_t enable, void* stream);
  *            (default); at most 6e7.
  *   test_hold_stage  for tests of that time-out path only: when > 0, the loader warp of CTA 0
  *            never signals the arrival of its stage number test_hold_stage (counted from 1),
- *            so the waits on it run out; 0 = off (default). */
+ *            so the waits on it run out; 0 = off (default).
+ *   inner_chunk  streamed 128-blocks per chunk of the single-problem schedule: chunk by
+ *            chunk, every CTA takes an equal share of the chunk's (row block, streamed block)
+ *            pairs, so that the CTAs read the same streamed-side images at about the same time
+ *            and find them in L2. 0 = automatic (default): one chunk unless the streamed-side
+ *            images of all blocks exceed 32 MiB. A forced value may lower the number of CTAs
+ *            (each CTA needs a pair in every chunk). Results are the same up to summation order.
+ *            At least 0. */
 typedef struct {
   int32_t seg_len;
   int32_t grid;
   int32_t wait_limit_us;
   int32_t test_hold_stage;
-  int32_t reserved[4];
+  int32_t inner_chunk;
+  int32_t reserved[3];
 } sense_tuning;
 
 int sense_plan_get_tuning(sense_plan plan, sense_tuning* out);

@@ -74,14 +74,17 @@ extern "C" int sense_plan_get_tuning(sense_plan P, sense_tuning* out) {
   out->grid = P->tc_grid_req == P->num_sms ? 0 : P->tc_grid_req;
   out->wait_limit_us = P->tc_wait_us;
   out->test_hold_stage = P->tc_test_hold;
+  out->inner_chunk = P->tc_inner_chunk;
   return SENSE_OK;
 }
 
 extern "C" int sense_plan_set_tuning(sense_plan P, const sense_tuning* t) {
   if (!P || !t) return set_error(SENSE_EINVAL, "null plan or tuning");
-  if (t->wait_limit_us < 0 || t->wait_limit_us > 60000000 || t->test_hold_stage < 0)
-    return set_error(SENSE_EINVAL, "wait_limit_us must be 0..6e7 and test_hold_stage >= 0");
-  const int rc = tc_set_tuning(P, t->seg_len, t->grid);
+  if (t->wait_limit_us < 0 || t->wait_limit_us > 60000000 || t->test_hold_stage < 0 ||
+      t->inner_chunk < 0)
+    return set_error(SENSE_EINVAL,
+                     "wait_limit_us must be 0..6e7, test_hold_stage and inner_chunk >= 0");
+  const int rc = tc_set_tuning(P, t->seg_len, t->grid, t->inner_chunk);
   if (rc != SENSE_OK) return rc;
   P->tc_wait_us = t->wait_limit_us;
   P->tc_wait_cycles = (long long)t->wait_limit_us * (P->clock_khz / 1000);

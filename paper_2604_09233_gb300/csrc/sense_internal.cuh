@@ -28,6 +28,10 @@ struct NvtxRange {
 constexpr int TILE = 128;
 constexpr int MAX_RP = 20;   // max basis rows kept in the FP32 bilinear part
 constexpr int MAX_CP = 64;   // max (padded) coils
+// Streamed-side image bytes that one stream-K chunk of the tensor-core passes may span: a
+// quarter of the 126 MB L2, so that the CTAs (which drift apart by part of a chunk) find the
+// images of the chunk they share in L2 instead of re-reading them from HBM.
+constexpr long long TC_L2_CHUNK_BYTES = 32ll << 20;
 
 // Device scalars of the CG recurrence (double), indices into plan->scal.
 enum ScalarSlot {
@@ -134,8 +138,12 @@ struct sense_plan_s {
   int min_rt = 0;                  // lower bound on RT (uniform kernels across a batch)
   int64_t geom_version = 0;        // incremented whenever the geometry arrays are rebuilt
   int tc_slots_e = 1, tc_slots_a = 1;
-  int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [nsb] stream-K slots of E
-  int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [nvb] stream-K slots of E^H
+  // stream-K slot tables of E / E^H: slot of (chunk c, row block o, CTA i) =
+  // slot_base[c * n_outer + o] + i; partial slots per row block
+  int *tc_first_e = nullptr, *tc_nslot_e = nullptr;  // [chunks_e][nsb], [nsb]
+  int *tc_first_a = nullptr, *tc_nslot_a = nullptr;  // [chunks_a][nvb], [nvb]
+  int tc_chunk_e = 1, tc_chunk_a = 1;              // streamed blocks per chunk
+  int tc_inner_chunk = 0;                          // forced chunk width (0: automatic)
   uint8_t* Qimg = nullptr;         // B image of S o p   [nvb][2][2][2Cp][128 B]
   uint8_t* Yimg = nullptr;         // B image of Sigma   [nsb][2][2][2Cp][128 B]
   float *qscale = nullptr, *yscale = nullptr;  // [Cp] per-coil unscale factors
@@ -209,7 +217,7 @@ int tc_encode(sense_plan_s* P, int prec, const float2* p_plan, float2* Y_int, fl
 int tc_adjoint(sense_plan_s* P, int prec, const float2* Y_int, float2* q, bool colmax_ready,
                const double* stop, cudaStream_t st);
 int tc_check_error(sense_plan_s* P);
-int tc_set_tuning(sense_plan_s* P, int seg_len, int grid);
+int tc_set_tuning(sense_plan_s* P, int seg_len, int grid, int inner_chunk);
 
 // diagnostics (sense_diag.cu) ----------------------------------------------------------
 enum KernelClass { KC_TC_ENC = 0, KC_TC_ADJ = 1, KC_F32_ENC = 2, KC_F32_ADJ = 3 };

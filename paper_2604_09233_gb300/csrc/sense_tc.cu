@@ -196,17 +196,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(Params p) {
         return true;
       };
       if (!queue) {
+        // chunk by chunk of streamed blocks, this CTA's share of the chunk's pairs
         const long long G = gridDim.x;
-        const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
-        const int n_inner = p.d0.n_inner;
-        int o = (int)(w0 / n_inner), in = (int)(w0 % n_inner);
-        for (long long w = w0; w < w1 && ok; ++w) {
-          const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
-                            ((w + 1 == w1 || in + 1 == n_inner) ? META_LAST : 0);
-          ok = push(0, o, in, flags, (int)(i - p.first_cta[o]));
-          if (++in == n_inner) {
-            in = 0;
-            ++o;
+        const int n_inner = p.d0.n_inner, n_outer = p.d0.n_outer;
+        const int CH = p.chunk_inner > 0 ? p.chunk_inner : n_inner;
+        for (int c0 = 0, c = 0; c0 < n_inner && ok; c0 += CH, ++c) {
+          const int wc = min(CH, n_inner - c0);
+          const long long Wc = (long long)n_outer * wc;
+          const long long w0 = i * Wc / G, w1 = (i + 1) * Wc / G;
+          int o = (int)(w0 / wc), in = (int)(w0 % wc);
+          for (long long w = w0; w < w1 && ok; ++w) {
+            const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
+                              ((w + 1 == w1 || in + 1 == wc) ? META_LAST : 0);
+            ok = push(0, o, c0 + in, flags, p.first_cta[(long long)c * n_outer + o] + (int)i);
+            if (++in == wc) {
+              in = 0;
+              ++o;
+            }
           }
         }
       } else {
@@ -704,21 +710,47 @@ __global__ void image_kernel(const float2* __restrict__ src, const float2* __res
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
-static int stream_k_layout(long long n_outer, long long n_inner, int G, std::vector<int>& first,
-                           std::vector<int>& nslot, int* max_slots) {
-  const long long W = n_outer * n_inner;
-  auto cta_of = [&](long long w) { return (int)(((w + 1) * G + W - 1) / W - 1); };
-  first.resize(n_outer);
-  nslot.resize(n_outer);
-  int mx = 1;
-  for (long long o = 0; o < n_outer; ++o) {
-    const int a = cta_of(o * n_inner), b = cta_of((o + 1) * n_inner - 1);
-    first[o] = a;
-    nslot[o] = b - a + 1;
-    mx = std::max(mx, b - a + 1);
+// Stream-K over chunks of `ch` streamed blocks: chunk by chunk, CTA i takes the pairs
+// [iW/G, (i+1)W/G) of the chunk's (row block, streamed block) space (W = n_outer x chunk
+// width). Per row block: its partial slots summed over the chunks; per (chunk, row block): the
+// slot base = the row block's slots in earlier chunks minus its first CTA in this chunk, so
+// the slot of CTA i is base + i. Every CTA range of a chunk must be non-empty (W >= G): then
+// all CTAs between the first and the last contributor of a row block write their slot, and
+// the reduction never reads a slot nobody wrote.
+static int stream_k_layout(long long n_outer, long long n_inner, long long ch, int G,
+                           std::vector<int>& base, std::vector<int>& nslot, int* max_slots) {
+  const long long nch = (n_inner + ch - 1) / ch;
+  base.assign((size_t)(nch * n_outer), 0);
+  nslot.assign((size_t)n_outer, 0);
+  for (long long c = 0; c < nch; ++c) {
+    const long long wc = std::min(ch, n_inner - c * ch);
+    const long long W = n_outer * wc;
+    auto cta_of = [&](long long w) { return (int)(((w + 1) * G + W - 1) / W - 1); };
+    for (long long o = 0; o < n_outer; ++o) {
+      const int a = cta_of(o * wc), b = cta_of((o + 1) * wc - 1);
+      base[(size_t)(c * n_outer + o)] = nslot[(size_t)o] - a;
+      nslot[(size_t)o] += b - a + 1;
+    }
   }
+  int mx = 1;
+  for (int v : nslot) mx = std::max(mx, v);
   *max_slots = mx;
   return SENSE_OK;
+}
+
+// Streamed blocks per stream-K chunk: all of them unless their streamed-side images (B image
+// of both stages, hi and lo, plus the phase operand; an upper bound) exceed TC_L2_CHUNK_BYTES,
+// then equal chunks below that size, as long as every chunk still gives each of the G CTAs
+// at least one pair.
+static long long chunk_for(const sense_plan_s* P, long long n_outer, long long n_inner, int G) {
+  const long long per_block = 2LL * 2 * 2 * P->Cp * 128 + 16384;
+  long long nch = (n_inner * per_block + TC_L2_CHUNK_BYTES - 1) / TC_L2_CHUNK_BYTES;
+  if (nch <= 1) return n_inner;
+  const long long ch = (n_inner + nch - 1) / nch;
+  nch = (n_inner + ch - 1) / ch;
+  const long long last = n_inner - (nch - 1) * ch;
+  if (n_outer * last < G) return n_inner;
+  return ch;
 }
 
 template <int MODE, int CP, int RP, int NPART, bool STORED = false>
@@ -795,8 +827,22 @@ static int tc_layout(sense_plan_s* P) {
   // their partial slot, so the reduction never reads a slot nobody wrote.
   P->tc_grid = (int)std::min<long long>(P->tc_grid, (long long)P->nsb * P->nvb);
   std::vector<int> fe, ne, fa, na;
-  stream_k_layout(P->nsb, P->nvb, P->tc_grid, fe, ne, &P->tc_slots_e);
-  stream_k_layout(P->nvb, P->nsb, P->tc_grid, fa, na, &P->tc_slots_a);
+  auto pick = [&](long long n_outer, long long n_inner) -> long long {
+    if (P->tc_inner_chunk > 0) return std::min<long long>(P->tc_inner_chunk, n_inner);
+    return chunk_for(P, n_outer, n_inner, P->tc_grid);
+  };
+  P->tc_chunk_e = (int)pick(P->nsb, P->nvb);
+  P->tc_chunk_a = (int)pick(P->nvb, P->nsb);
+  // every chunk must give each CTA at least one pair (a forced chunk width may need fewer CTAs)
+  auto min_pairs = [](long long n_outer, long long n_inner, long long ch) {
+    const long long nch = (n_inner + ch - 1) / ch;
+    return n_outer * std::min(ch, n_inner - (nch - 1) * ch);
+  };
+  P->tc_grid = (int)std::min<long long>(
+      P->tc_grid, std::min(min_pairs(P->nsb, P->nvb, P->tc_chunk_e),
+                           min_pairs(P->nvb, P->nsb, P->tc_chunk_a)));
+  stream_k_layout(P->nsb, P->nvb, P->tc_chunk_e, P->tc_grid, fe, ne, &P->tc_slots_e);
+  stream_k_layout(P->nvb, P->nsb, P->tc_chunk_a, P->tc_grid, fa, na, &P->tc_slots_a);
   auto up = [&](int** d, const std::vector<int>& h) -> int {
     if (cudaMalloc((void**)d, h.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
@@ -851,15 +897,16 @@ void tc_free(sense_plan_s* P) {
   cudaFree(P->yscale); cudaFree(P->colmax); cudaFree(P->tc_err);
 }
 
-int tc_set_tuning(sense_plan_s* P, int seg_len, int grid) {
-  if (seg_len < 1 || seg_len > 64 || grid < 0 || grid > 64 * P->num_sms)
-    return set_error(SENSE_EINVAL, "seg_len must be 1..64 and grid 0..64 x SMs");
+int tc_set_tuning(sense_plan_s* P, int seg_len, int grid, int inner_chunk) {
+  if (seg_len < 1 || seg_len > 64 || grid < 0 || grid > 64 * P->num_sms || inner_chunk < 0)
+    return set_error(SENSE_EINVAL, "seg_len must be 1..64, grid 0..64 x SMs, inner_chunk >= 0");
   const int g = grid == 0 ? P->num_sms : grid;
   P->tc_seg_len = seg_len;
-  if (g != P->tc_grid_req) {
+  if (g != P->tc_grid_req || inner_chunk != P->tc_inner_chunk) {
     SENSE_CUDA_TRY(cudaDeviceSynchronize());
     P->tc_grid_req = g;
     P->tc_grid = g;
+    P->tc_inner_chunk = inner_chunk;
     return tc_layout(P);
   }
   return SENSE_OK;
@@ -995,6 +1042,7 @@ static int run_pass(sense_plan_s* P, int mode, int npart, const uint8_t* img, co
   d.ph_unscale = P->ph_unscale;
   prm.inst = nullptr;
   prm.first_cta = enc ? P->tc_first_e : P->tc_first_a;
+  prm.chunk_inner = enc ? P->tc_chunk_e : P->tc_chunk_a;
   prm.W = (long long)d.n_outer * d.n_inner;
   prm.err = P->tc_err;
   prm.stop = stop;
@@ -1123,6 +1171,7 @@ int tc_store_p(sense_plan_s* P, bool enable, cudaStream_t st) {
       d.n_inner = enc ? P->nvb : P->nsb;
       d.chunk = d.n_inner;
       prm.first_cta = enc ? P->tc_first_e : P->tc_first_a;
+      prm.chunk_inner = enc ? P->tc_chunk_e : P->tc_chunk_a;
       prm.W = (long long)d.n_outer * d.n_inner;
       prm.err = P->tc_err;
       prm.seg_len = P->tc_seg_len;

@@ -36,9 +36,12 @@ struct InstDesc {
 };
 
 // Two schedules feed the same kernel:
-//   stream-K (one instance, inst == nullptr): CTA i takes the pairs [iW/G, (i+1)W/G) of the
-//     flattened (row block, streamed block) space; a row block's partial slot is
-//     i - first_cta[row block];
+//   stream-K (one instance, inst == nullptr): the streamed blocks are cut into chunks of
+//     `chunk_inner` (one chunk unless the streamed-side images of all blocks exceed an L2
+//     budget); chunk by chunk, CTA i takes the pairs [iW/G, (i+1)W/G) of the chunk's
+//     flattened (row block, streamed block) space, so all CTAs read the same chunk's images
+//     at about the same time; the partial slot of (chunk c, row block o) is
+//     first_cta[c * n_outer + o] + i;
 //   work queue (inst != nullptr): CTAs claim items {instance, row block, first, end streamed
 //     block} with an atomic counter (zeroed before the launch), skipping stopped instances;
 //     an item is one run and its slot is first / chunk.
@@ -48,7 +51,8 @@ struct Params {
   const int4* items;     // work queue: [n_items]
   unsigned* next;        // work queue: claim counter
   int n_items;
-  const int* first_cta;  // stream-K: [n_outer]
+  const int* first_cta;  // stream-K: slot base [chunks][n_outer] (slot = base + CTA index)
+  int chunk_inner;       // stream-K: streamed blocks per chunk (n_inner: one chunk)
   long long W;           // stream-K: n_outer * n_inner
   int* err;              // device error word (nonzero after a time-out)
   const double* stop;    // stream-K: CG stop flag (nullable)

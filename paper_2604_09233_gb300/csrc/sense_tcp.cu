@@ -217,17 +217,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
         return true;
       };
       if (!queue) {
+        // chunk by chunk of streamed blocks, this CTA's share of the chunk's pairs
         const long long G = gridDim.x;
-        const long long w0 = i * p.W / G, w1 = (i + 1) * p.W / G;
-        const int n_inner = p.d0.n_inner;
-        int o = (int)(w0 / n_inner), in = (int)(w0 % n_inner);
-        for (long long w = w0; w < w1 && ok; ++w) {
-          const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
-                            ((w + 1 == w1 || in + 1 == n_inner) ? META_LAST : 0);
-          ok = push(0, o, in, flags, (int)(i - p.first_cta[o]));
-          if (++in == n_inner) {
-            in = 0;
-            ++o;
+        const int n_inner = p.d0.n_inner, n_outer = p.d0.n_outer;
+        const int CH = p.chunk_inner > 0 ? p.chunk_inner : n_inner;
+        for (int c0 = 0, c = 0; c0 < n_inner && ok; c0 += CH, ++c) {
+          const int wc = min(CH, n_inner - c0);
+          const long long Wc = (long long)n_outer * wc;
+          const long long w0 = i * Wc / G, w1 = (i + 1) * Wc / G;
+          int o = (int)(w0 / wc), in = (int)(w0 % wc);
+          for (long long w = w0; w < w1 && ok; ++w) {
+            const int flags = ((w == w0 || in == 0) ? META_FIRST : 0) |
+                              ((w + 1 == w1 || in + 1 == wc) ? META_LAST : 0);
+            ok = push(0, o, c0 + in, flags, p.first_cta[(long long)c * n_outer + o] + (int)i);
+            if (++in == wc) {
+              in = 0;
+              ++o;
+            }
           }
         }
       } else {

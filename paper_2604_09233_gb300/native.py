@@ -56,7 +56,7 @@ KERNEL_CLASSES = ["tc_encode_pass", "tc_adjoint_pass", "fp32_encode", "fp32_adjo
 class Tuning(ctypes.Structure):
     _fields_ = [("seg_len", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("wait_limit_us", ctypes.c_int32), ("test_hold_stage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("inner_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Problem(ctypes.Structure):
@@ -563,11 +563,13 @@ def sense_plan_get_tuning(plan):
     t = Tuning()
     _check(_lib.sense_plan_get_tuning(plan, ctypes.byref(t)), "sense_plan_get_tuning")
     return {"seg_len": t.seg_len, "grid": t.grid, "wait_limit_us": t.wait_limit_us,
-            "test_hold_stage": t.test_hold_stage}
+            "test_hold_stage": t.test_hold_stage, "inner_chunk": t.inner_chunk}
 
 
-def sense_plan_set_tuning(plan, seg_len=4, grid=0, wait_limit_us=0, test_hold_stage=0):
-    t = Tuning(int(seg_len), int(grid), int(wait_limit_us), int(test_hold_stage))
+def sense_plan_set_tuning(plan, seg_len=4, grid=0, wait_limit_us=0, test_hold_stage=0,
+                          inner_chunk=0):
+    t = Tuning(int(seg_len), int(grid), int(wait_limit_us), int(test_hold_stage),
+               int(inner_chunk))
     _check(_lib.sense_plan_set_tuning(plan, ctypes.byref(t)), "sense_plan_set_tuning")
 
 
