@@ -263,13 +263,13 @@ def run_reference(args):
 # by the SHA-256 of the pass-kernel source they were taken on (pass_kernel_source_hash); any other
 # source reports null.
 KERNEL_TRAFFIC = {
-    "107444c196ea2e131360d5f0358822b824876fd08b6a37e4b5457b5076af4bd8": {
+    "8658eb9a2ffd27120f5d7929217a8e3229133744df14218da7c3be6cddba2ac9": {
         "2d_256x256_32coil_35750samp_sh3": {
             "precision": "tc_split",
-            "tc_encode_pass": 174737920 + 9260800,
-            "tc_adjoint_pass": 190799872 + 444672,
-            "inst_tc_encode_pass": 1485124734,
-            "inst_tc_adjoint_pass": 1511146539,
+            "tc_encode_pass": 175291904 + 9222400,
+            "tc_adjoint_pass": 190544896 + 379136,
+            "inst_tc_encode_pass": 1485252632,
+            "inst_tc_adjoint_pass": 1511248085,
         },
     },
 }
