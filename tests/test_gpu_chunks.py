@@ -102,3 +102,24 @@ def test_negative_chunk_is_rejected(case):
     with pytest.raises(native.SenseError):
         native.sense_plan_set_tuning(plan.handle, inner_chunk=-1)
     assert native.sense_plan_get_tuning(plan.handle)["inner_chunk"] == 0
+
+
+def test_stored_tiles_under_forced_chunks(case):
+    """Stored-P mode with a forced chunk width: the tiles are kept per (row block, streamed
+    block) pair, so the stored passes reproduce the generated passes of the same schedule bit
+    for bit, and stay within the bar of the oracle."""
+    from paper_2604_09233_gb300 import native
+    wl, plan, ref, one, run = case
+    native.sense_plan_set_tuning(plan.handle, inner_chunk=3)
+    try:
+        gen = run()
+        native.sense_plan_store_p(plan.handle, True)
+        try:
+            st = run()
+        finally:
+            native.sense_plan_store_p(plan.handle, False)
+        for k in ("E", "EH", "EHE"):
+            assert np.array_equal(st[k], gen[k]), k
+            assert _rel(st[k], ref[k]) <= TOL, k
+    finally:
+        native.sense_plan_set_tuning(plan.handle)
