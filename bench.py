@@ -270,6 +270,11 @@ KERNEL_TRAFFIC = {
             "tc_adjoint_pass": 190544896 + 379136,
             "inst_tc_encode_pass": 1485252632,
             "inst_tc_adjoint_pass": 1511248085,
+            # stored-P passes (the NKP = 0 instantiation of the same source): one capture of
+            # `python bench.py --op-only --stored --steps 1 --warmup 1`
+            # (profiles/tcp_pass_stored_2d256_32coil.md)
+            "stored_tc_encode_pass": 19950000000 + 13360000,
+            "stored_tc_adjoint_pass": 19560000000 + 609790,
         },
     },
 }
