@@ -32,7 +32,7 @@ struct sense_batch_s {
   int n_items[2] = {0, 0};
   unsigned* qnext = nullptr;       // [2] claim counters
   int* err = nullptr;              // time-out word of the batched passes
-  std::vector<float2*> ypart, xpart;   // per instance [nchunk][Kp][Cp], [nchunk][Lp]
+  std::vector<float2*> ypart, xpart;   // per instance [nchunk][Kp][Cp], [nchunk][Lp][xpart coils]
   std::vector<int*> nslot_e, nslot_a;  // per instance, per row block: nchunk
   cudaGraphExec_t gexec = nullptr;
   int graph_prec = -1;
@@ -98,7 +98,8 @@ int build_layout(sense_batch_s* B) {
     int *ne = nullptr, *na = nullptr;
     if ((rc = dmalloc((void**)&yp, (size_t)nch_e * P->Kp * P->Cp * 8, "batch partials")) ||
         (B->ypart.push_back(yp), 0) ||
-        (rc = dmalloc((void**)&xp, (size_t)nch_a * P->Lp * 8, "batch partials")) ||
+        (rc = dmalloc((void**)&xp, (size_t)nch_a * P->Lp * tc_xpart_coils(P) * 8,
+                      "batch partials")) ||
         (B->xpart.push_back(xp), 0) ||
         (rc = dmalloc((void**)&ne, (size_t)P->nsb * 4, "batch slots")) ||
         (B->nslot_e.push_back(ne), 0) ||

@@ -149,7 +149,7 @@ struct sense_plan_s {
   float *qscale = nullptr, *yscale = nullptr;  // [Cp] per-coil unscale factors
   unsigned* colmax = nullptr;      // [2][Cp] per-coil maxima (float bits)
   float2* Ypart_tc = nullptr;      // [tc_slots_e][Kp][Cp]
-  float2* Xpart_tc = nullptr;      // [tc_slots_a][Lp]
+  float2* Xpart_tc = nullptr;      // [tc_slots_a][Lp][tc_xpart_coils]
   int* tc_err = nullptr;           // time-out word written by the tensor-core kernels
   uint4* p_enc = nullptr;          // stored-P mode: phase tiles of the E pass
   uint4* p_adj = nullptr;          // and of the E^H pass (conjugated, transposed)

@@ -811,6 +811,8 @@ int tc_launch(sense_plan_s* P, int mode, int npart, int cp, int rt, const tc::Pa
                     : dispatch_cp<tc::ADJ, 1>(P, cp, rt, prm, G, st, stored);
 }
 
+int tc_xpart_coils(const sense_plan_s* P) { return tc::tcp_covers(P->Cp, false) ? P->Cp : 1; }
+
 static void tc_free_layout(sense_plan_s* P) {
   cudaFree(P->tc_first_e); cudaFree(P->tc_nslot_e); cudaFree(P->tc_first_a);
   cudaFree(P->tc_nslot_a); cudaFree(P->Ypart_tc); cudaFree(P->Xpart_tc);
@@ -857,7 +859,8 @@ static int tc_layout(sense_plan_s* P) {
   if ((rc = up(&P->tc_first_a, fa)) != SENSE_OK) return rc;
   if ((rc = up(&P->tc_nslot_a, na)) != SENSE_OK) return rc;
   if (cudaMalloc((void**)&P->Ypart_tc, (size_t)P->tc_slots_e * P->Kp * P->Cp * 8) != cudaSuccess ||
-      cudaMalloc((void**)&P->Xpart_tc, (size_t)P->tc_slots_a * P->Lp * 8) != cudaSuccess) {
+      cudaMalloc((void**)&P->Xpart_tc, (size_t)P->tc_slots_a * P->Lp * tc_xpart_coils(P) * 8) !=
+          cudaSuccess) {
     cudaGetLastError();
     return set_error(SENSE_ENOMEM, "tc partial buffers");
   }
@@ -954,6 +957,31 @@ __global__ void tc_reduce_y_kernel(const float2* __restrict__ Ypart, const int* 
 }
 
 // q[l] = sum over the stream-K slots of voxel block l/128
+// q[l] = sum over the voxel block's slots and the coils of conj(S(l, c)) X(l, c) (Eq. 5's coil
+// combine; S includes j): the phase kernel writes per-coil partial rows.
+__global__ void tc_reduce_xc_kernel(const float2* __restrict__ Xpart, const int* __restrict__ nslot,
+                                    const float2* __restrict__ S, long long Lp, int Cp,
+                                    float2* __restrict__ q, const double* __restrict__ stop) {
+  if (stop && *stop != 0.0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Lp;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ns = nslot[i / TILE];
+    float2 a = make_float2(0.f, 0.f);
+    for (int c = 0; c < Cp; ++c) {
+      float2 x = make_float2(0.f, 0.f);
+      for (int s = 0; s < ns; ++s) {
+        const float2 v = Xpart[((long long)s * Lp + i) * Cp + c];
+        x.x += v.x;
+        x.y += v.y;
+      }
+      const float2 sv = S[i * Cp + c];
+      a.x = fmaf(sv.x, x.x, fmaf(sv.y, x.y, a.x));
+      a.y = fmaf(sv.x, x.y, fmaf(-sv.y, x.x, a.y));
+    }
+    q[i] = a;
+  }
+}
+
 __global__ void tc_reduce_x_kernel(const float2* __restrict__ Xpart, const int* __restrict__ nslot,
                                    long long Lp, float2* __restrict__ q,
                                    const double* __restrict__ stop) {
@@ -987,7 +1015,10 @@ int tc_reduce_y(sense_plan_s* P, const float2* Ypart, const int* nslot, float2* 
 
 int tc_reduce_x(sense_plan_s* P, const float2* Xpart, const int* nslot, float2* q,
                 const double* stop, cudaStream_t st) {
-  tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(Xpart, nslot, P->Lp, q, stop);
+  if (tc_xpart_coils(P) > 1)
+    tc_reduce_xc_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(Xpart, nslot, P->S, P->Lp, P->Cp, q, stop);
+  else
+    tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(Xpart, nslot, P->Lp, q, stop);
   SENSE_CUDA_TRY(cudaGetLastError());
   count_launch(P);
   return SENSE_OK;

@@ -14,8 +14,9 @@ struct InstDesc {
   const float* colAnc;   // [n_outer][cols_total] (Aanc for ENC, Banc for ADJ)
   const uint8_t* Bimg;   // [n_inner][2 halves][NPART][2*CP rows][128 B]
   const float* bscale;   // [CP] 2^-e unscale per coil
-  const float2* S;       // [rows_total][CP] (ADJ epilogue)
-  float2* out;           // ENC: [slots][rows_total][CP]; ADJ: [slots][rows_total]
+  const float2* S;       // [rows_total][CP] (ADJ epilogue of the 64-coil kernel)
+  float2* out;           // ENC: [slots][rows_total][CP]; ADJ: the same for the phase kernel,
+                         // [slots][rows_total] (coils combined) for the 64-coil kernel
   const double* stop;    // CG stop flag of the instance (nullable; work queue only)
   long long rows_total, cols_total;
   int n_outer, n_inner;
@@ -99,6 +100,9 @@ int tc_make_image(sense_plan_s* P, int npart, const float2* src, const float2* p
 // sample block; q from Xpart [slots][Lp] with nslot per voxel block.
 int tc_reduce_y(sense_plan_s* P, const float2* Ypart, const int* nslot, float2* Y_int,
                 float2* s_user, unsigned* colmax, const double* stop, cudaStream_t st);
+// Values per partial row of the E^H pass: Cp (the phase kernel writes per-coil rows; the coil
+// combine happens in tc_reduce_x) or 1 (the 64-coil kernel combines the coils itself).
+int tc_xpart_coils(const sense_plan_s* P);
 int tc_reduce_x(sense_plan_s* P, const float2* Xpart, const int* nslot, float2* q,
                 const double* stop, cudaStream_t st);
 

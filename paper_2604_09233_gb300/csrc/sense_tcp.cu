@@ -68,7 +68,7 @@ template <int CP, int NPART, int NKP>
 constexpr size_t smem_bytes() {
   using LY = Lay<CP, NPART, NKP>;
   return 1024 + LY::NBUF * (LY::B_BYTES + LY::PC_BYTES) + 2 * LY::PR_BYTES +
-         2 * LY::NBUF * 128 * 4 + 4 * 128 * 8 + (CP / 4) * NGEN_WARPS * 32 * 8 +
+         2 * LY::NBUF * 128 * 4 + (CP / 4) * NGEN_WARPS * 32 * 8 +
          LY::NBUF * sizeof(Meta) + 40 * 8 + 16;
 }
 
@@ -89,8 +89,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   uint8_t* sPr = sPc + NBUF * LY::PC_BYTES;               // [2][PR_BYTES]
   float* sAnc = (float*)(sPr + 2 * LY::PR_BYTES);         // [NBUF][128] streamed anchors
   float* sRowAnc = sAnc + NBUF * 128;                     // [NBUF][128] row anchors
-  float2* sRed = (float2*)(sRowAnc + NBUF * 128);         // [4][128]
-  float2* sRacc = sRed + 4 * 128;                         // [CP/4][512]
+  float2* sRacc = (float2*)(sRowAnc + NBUF * 128);        // [CP/4][512]
   Meta* sMeta = (Meta*)(sRacc + CW * NGEN_WARPS * 32);    // [NBUF]
   uint64_t* bars = (uint64_t*)(sMeta + NBUF);
   uint64_t* full = bars;                 // [NBUF] streamed block landed
@@ -103,9 +102,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   uint64_t* afull = tempty + NSLOT;      // accumulator full
   uint64_t* aempty = afull + 1;          // accumulator drained
   uint64_t* drain = aempty + 1;          // [3] final MMA drain of each issuing warp
-  uint64_t* ered = drain + 3;            // ADJ epilogue: partial sums written
-  uint64_t* edone = ered + 1;            // ADJ epilogue: partial sums consumed
-  uint32_t* tmem_slot = (uint32_t*)(edone + 1);
+  uint32_t* tmem_slot = (uint32_t*)(drain + 3);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -134,8 +131,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     mbar_init(smem_u32(afull), 2);
     mbar_init(smem_u32(aempty), NGEN_WARPS);
     for (int r = 0; r < 3; ++r) mbar_init(smem_u32(drain + r), 1);
-    mbar_init(smem_u32(ered), NGEN_WARPS);
-    mbar_init(smem_u32(edone), 4);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -442,7 +437,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     };
     Ring<NBUF> rb;
     Ring<NSLOT> rs;
-    int seg = 0, run = 0, seg_pos = 0;  // segments, runs; position of the block in its segment
+    int seg = 0, seg_pos = 0;  // segments drained; position of the block in its segment
     bool ok = true;
     // the next block's data / the next stage's phases, found ready by a test made during the
     // previous stage's arithmetic (so that the test's latency is hidden behind it)
@@ -453,7 +448,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     int d_b = 0, d_slot = 0;
     long long d_row = 0;
     // Add the segment accumulators to the running sums (the E^H pass generated e^{+i phi}:
-    // its conjugate is taken here); at the end of a run also write the run's output.
+    // its conjugate is taken here); at the end of a run also write the run's output: per row
+    // and coil for both passes.
     auto drain = [&]() -> bool {
       drain_due = false;
       if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7, LIM)) return false;
@@ -482,49 +478,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       ++seg;
       if (!d_out) return true;
       // ---------------------------------------------------------------- run output
+      // this warp's coils of the run's rows, unscaled (the E^H pass's coil combine with S,
+      // Eq. 5, is done when the partial slots are summed)
       const InstDesc& d = desc(d_b);
-      if (MODE == ENC) {
-        float2* dst = d.out + ((long long)d_slot * d.rows_total + d_row) * CP + cbase;
+      float2* dst = d.out + ((long long)d_slot * d.rows_total + d_row) * CP + cbase;
 #pragma unroll
-        for (int c = 0; c < CW; ++c) {
-          const float sc = d.bscale[cbase + c];
-          const float2 a = racc[c * NGT];
-          dst[c] = make_float2(a.x * sc, a.y * sc);
-        }
-      } else {
-        const float2* Srow = d.S + d_row * CP + cbase;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-          const float sc = d.bscale[cbase + c];
-          const float2 a = racc[c * NGT];
-          const float xr = a.x * sc, xi = a.y * sc;
-          const float2 sv = Srow[c];
-          acc.x = fmaf(sv.x, xr, fmaf(sv.y, xi, acc.x));
-          acc.y = fmaf(sv.x, xi, fmaf(-sv.y, xr, acc.y));
-        }
-        // combine the four warpgroups' coil ranges through shared memory
-        if (run > 0 &&
-            !warp_wait(smem_u32(edone), (uint32_t)(run - 1) & 1u, abort_flag, p.err, 8, LIM))
-          return false;
-        sRed[g * 128 + row] = acc;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(ered));
-        if (g == 0) {
-          if (!warp_wait(smem_u32(ered), (uint32_t)run & 1u, abort_flag, p.err, 8, LIM)) return false;
-          float2 v = sRed[row];
-          for (int k = 1; k < 4; ++k) {
-            v.x += sRed[k * 128 + row].x;
-            v.y += sRed[k * 128 + row].y;
-          }
-          d.out[(long long)d_slot * d.rows_total + d_row] = v;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(edone));
-        }
+      for (int c = 0; c < CW; ++c) {
+        const float sc = d.bscale[cbase + c];
+        const float2 a = racc[c * NGT];
+        dst[c] = make_float2(a.x * sc, a.y * sc);
       }
 #pragma unroll
       for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
-      ++run;
       return true;
     };
     for (;; rb.next()) {
