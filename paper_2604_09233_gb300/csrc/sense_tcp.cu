@@ -72,8 +72,9 @@ constexpr size_t smem_bytes() {
          LY::NBUF * sizeof(Meta) + 40 * 8 + 16;
 }
 
-template <int MODE, int CP, int NPART, int NKP>
-// 18 warps, one CTA per SM (see sense_tc.cu for the register budget).
+// EMIT: also write every generated tile to Params::emit (the pass that builds the stored-P
+// tiles); the ordinary passes are compiled without that code.
+template <int MODE, int CP, int NPART, int NKP, bool EMIT>
 __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   using LY = Lay<CP, NPART, NKP>;
   constexpr int NBUF = LY::NBUF;
@@ -509,8 +510,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       const float* anc = sAnc + buf * 128;
       const float ranc = sRowAnc[buf * 128 + row];
       const float2 rb2 = make_float2(ranc, ranc);
-      uint4* emit = p.emit ? p.emit + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
-                           : nullptr;
+      uint4* emit = EMIT ? p.emit + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
+                         : nullptr;
       // stored tiles of this pair: 16 chunks (stage, warpgroup, half) of [4][128] uint4
       const uint4* ptile =
           STORED ? dm.stored + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
             tmem_st4(hcol + 32, re_lo);
             tmem_st4(hcol + 64, im_hi);
             tmem_st4(hcol + 96, im_lo);
-            if (emit) {
+            if (EMIT) {
               uint4* dst = emit + (((st * 4 + g) * 2 + jh) * 4) * 128;
               dst[0] = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
               dst[128] = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
@@ -662,18 +663,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   }
 }
 
+template <int MODE, int CP, int NPART, int NKP, bool EMIT>
+static int set_smem() {
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    SENSE_CUDA_TRY(cudaFuncSetAttribute(tcp_pass_kernel<MODE, CP, NPART, NKP, EMIT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_bytes<CP, NPART, NKP>()));
+    attr_set = true;
+  }
+  return SENSE_OK;
+}
+
 template <int MODE, int CP, int NPART, int NKP>
 static int launch(sense_plan_s* P, const Params& prm, int G, cudaStream_t st) {
   constexpr size_t smem = smem_bytes<CP, NPART, NKP>();
   static_assert(smem <= 232448, "shared memory of the tensor-core phase kernel");
-  auto kern = tcp_pass_kernel<MODE, CP, NPART, NKP>;
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    SENSE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    attr_set = true;
-  }
-  int rc = prof_begin(P, MODE == ENC ? KC_TC_ENC : KC_TC_ADJ, st);
+  // tiles are emitted only by a generating split pass (the stored-P set-up)
+  constexpr bool CAN_EMIT = NPART == 2 && NKP > 0;
+  const bool emit = CAN_EMIT && prm.emit != nullptr;
+  if (!CAN_EMIT && prm.emit != nullptr)
+    return set_error(SENSE_EUNSUPPORTED, "tile emission needs a generating split pass");
+  auto kern = emit ? tcp_pass_kernel<MODE, CP, NPART, NKP, CAN_EMIT>
+                   : tcp_pass_kernel<MODE, CP, NPART, NKP, false>;
+  int rc = emit ? set_smem<MODE, CP, NPART, NKP, CAN_EMIT>()
+                : set_smem<MODE, CP, NPART, NKP, false>();
+  if (rc != SENSE_OK) return rc;
+  rc = prof_begin(P, MODE == ENC ? KC_TC_ENC : KC_TC_ADJ, st);
   if (rc != SENSE_OK) return rc;
   kern<<<G, NTHREADS, smem, st>>>(prm);
   SENSE_CUDA_TRY(cudaGetLastError());
