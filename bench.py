@@ -263,18 +263,13 @@ def run_reference(args):
 # by the SHA-256 of the pass-kernel source they were taken on (pass_kernel_source_hash); any other
 # source reports null.
 KERNEL_TRAFFIC = {
-    "8658eb9a2ffd27120f5d7929217a8e3229133744df14218da7c3be6cddba2ac9": {
+    "e076f38bb4391122a9cdb4d1d291b66f5b0b90e219d3fb6b0e1a3f12d9714084": {
         "2d_256x256_32coil_35750samp_sh3": {
             "precision": "tc_split",
-            "tc_encode_pass": 175291904 + 9222400,
-            "tc_adjoint_pass": 190544896 + 379136,
-            "inst_tc_encode_pass": 1485252632,
-            "inst_tc_adjoint_pass": 1511248085,
-            # stored-P passes (the NKP = 0 instantiation of the same source): one capture of
-            # `python bench.py --op-only --stored --steps 1 --warmup 1`
-            # (profiles/tcp_pass_stored_2d256_32coil.md)
-            "stored_tc_encode_pass": 19950000000 + 13360000,
-            "stored_tc_adjoint_pass": 19560000000 + 609790,
+            "tc_encode_pass": 174706432 + 8401152,
+            "tc_adjoint_pass": 169117184 + 9986560,
+            "inst_tc_encode_pass": 1420550033,
+            "inst_tc_adjoint_pass": 1420752711,
         },
     },
 }
