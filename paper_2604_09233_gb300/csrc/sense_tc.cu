@@ -958,27 +958,31 @@ __global__ void tc_reduce_y_kernel(const float2* __restrict__ Ypart, const int* 
 
 // q[l] = sum over the stream-K slots of voxel block l/128
 // q[l] = sum over the voxel block's slots and the coils of conj(S(l, c)) X(l, c) (Eq. 5's coil
-// combine; S includes j): the phase kernel writes per-coil partial rows.
+// combine; S includes j): the phase kernel writes per-coil partial rows. One thread per (voxel,
+// coil), so that the partial rows and S are read contiguously; the Cp coil lanes of a voxel
+// (Cp in {8, 16, 32} divides the warp) are summed with shuffles in a fixed order.
 __global__ void tc_reduce_xc_kernel(const float2* __restrict__ Xpart, const int* __restrict__ nslot,
                                     const float2* __restrict__ S, long long Lp, int Cp,
                                     float2* __restrict__ q, const double* __restrict__ stop) {
   if (stop && *stop != 0.0) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Lp;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long n = Lp * Cp;   // a multiple of 32: Lp is a multiple of 128
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t / Cp;
     const int ns = nslot[i / TILE];
-    float2 a = make_float2(0.f, 0.f);
-    for (int c = 0; c < Cp; ++c) {
-      float2 x = make_float2(0.f, 0.f);
-      for (int s = 0; s < ns; ++s) {
-        const float2 v = Xpart[((long long)s * Lp + i) * Cp + c];
-        x.x += v.x;
-        x.y += v.y;
-      }
-      const float2 sv = S[i * Cp + c];
-      a.x = fmaf(sv.x, x.x, fmaf(sv.y, x.y, a.x));
-      a.y = fmaf(sv.x, x.y, fmaf(-sv.y, x.x, a.y));
+    float2 x = make_float2(0.f, 0.f);
+    for (int s = 0; s < ns; ++s) {
+      const float2 v = Xpart[(long long)s * n + t];
+      x.x += v.x;
+      x.y += v.y;
     }
-    q[i] = a;
+    const float2 sv = S[t];
+    float ar = fmaf(sv.x, x.x, sv.y * x.y), ai = fmaf(sv.x, x.y, -sv.y * x.x);
+    for (int o = Cp >> 1; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if ((t & (Cp - 1)) == 0) q[i] = make_float2(ar, ai);
   }
 }
 
@@ -1016,7 +1020,8 @@ int tc_reduce_y(sense_plan_s* P, const float2* Ypart, const int* nslot, float2* 
 int tc_reduce_x(sense_plan_s* P, const float2* Xpart, const int* nslot, float2* q,
                 const double* stop, cudaStream_t st) {
   if (tc_xpart_coils(P) > 1)
-    tc_reduce_xc_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(Xpart, nslot, P->S, P->Lp, P->Cp, q, stop);
+    tc_reduce_xc_kernel<<<vgrid(P, P->Lp * P->Cp), 256, 0, st>>>(Xpart, nslot, P->S, P->Lp, P->Cp,
+                                                                   q, stop);
   else
     tc_reduce_x_kernel<<<vgrid(P, P->Lp), 256, 0, st>>>(Xpart, nslot, P->Lp, q, stop);
   SENSE_CUDA_TRY(cudaGetLastError());
