@@ -270,6 +270,11 @@ KERNEL_TRAFFIC = {
             "tc_adjoint_pass": 169117184 + 9986560,
             "inst_tc_encode_pass": 1420550033,
             "inst_tc_adjoint_pass": 1420752711,
+            # stored-P passes (the NKP = 0 instantiation of the same source): one capture of
+            # `python bench.py --op-only --stored --steps 1 --warmup 1`
+            # (profiles/tcp_pass_stored_2d256_32coil.md)
+            "stored_tc_encode_pass": 19920000000 + 13000000,
+            "stored_tc_adjoint_pass": 19570000000 + 18030000,
         },
     },
 }
