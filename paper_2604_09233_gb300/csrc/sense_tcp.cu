@@ -15,15 +15,20 @@
 // split into FP16 hi (+ lo) and write the tile over the phases; the MMA warp contracts it
 // with the B operand as before. The E^H pass writes the tile of e^{+i phi} and takes the
 // conjugate in the accumulator read-out.
-// Per CTA (one per SM, persistent):
-//   16 generator warps  : phases out of TMEM -> anchors -> sin/cos -> FP16 tile into TMEM;
-//   1 MMA warp          : the phase MMAs of stage g+1 (A and B in shared memory), then the
-//                         contraction MMAs of stage g (A in TMEM, B in shared memory);
+// Per CTA (one per SM, persistent, 20 warps):
+//   16 generator warps  : phases out of TMEM -> anchors -> sin/cos -> FP16 tile into TMEM; at
+//                         segment ends they drain the accumulators into running sums, and at
+//                         run ends write the run's rows per coil (both passes; the E^H pass's
+//                         coil combine with S is done by the slot reduction);
+//   1 phase warp        : the phase MMAs of the stages ahead (A and B in shared memory), each
+//                         into the TMEM slot of its stage once that slot's contraction is done;
+//   2 contraction warps : the contraction MMAs of each stage (A in TMEM, B in shared memory),
+//                         one warp per accumulator (the tile's real and imaginary parts);
 //   1 loader warp       : bulk copies of the B image, the streamed phase operand, the anchors
 //                         of every streamed block and the row phase operand of every run,
 //                         and the shared-memory metadata ring of the schedule.
-// Schedules (stream-K for one problem, a work queue for a batch), run/segment accumulation
-// and the epilogues are those of sense_tc.cu. Every wait is bounded.
+// Schedules: stream-K for one problem (two-level when the streamed-side images exceed an L2
+// budget), a work queue for a batch. Every wait is bounded.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   using LY = Lay<CP, NPART, NKP>;
   constexpr int NBUF = LY::NBUF;
   constexpr int NSLOT = LY::NSLOT;
-  constexpr int CW = CP / 4;  // coils per warpgroup in the epilogue
+  constexpr int CW = CP / 4;  // coils per warpgroup in the drains and the run output
   // NKP = 0: stored-P variant: the tiles are read from HBM (written by a generating pass with
   // Params::emit), no phase operands or anchors are loaded and no phase MMAs run
   constexpr bool STORED = NKP == 0;
