@@ -410,6 +410,21 @@ int sense_plan_stats(sense_plan plan, sense_stats* out);
  * second over `ms_budget` milliseconds of work (approximately). Errors: EINVAL, ECUDA. */
 int sense_diag_sincos_rate(double ms_budget, double* per_s);
 
+/* Host-only views of the single-problem schedule of the tensor-core passes (no device use).
+ * sense_diag_chunk_width: the streamed 128-blocks per stream-K chunk that a pass over n_outer
+ *   row blocks x n_inner streamed blocks with cp padded coils uses on g CTAs (automatic width:
+ *   n_inner unless the streamed-side images exceed 32 MiB). *width out. Errors: EINVAL.
+ * sense_diag_stream_k_layout: for chunks of `chunk` streamed blocks, chunk by chunk CTA i takes
+ *   the pairs [i W / g, (i + 1) W / g) of the chunk's (row block, streamed block) space (W =
+ *   n_outer x chunk width); the partial slot of (chunk c, row block o, CTA i) is
+ *   slot_base[c * n_outer + o] + i. Writes slot_base [ceil(n_inner / chunk)][n_outer], nslot
+ *   [n_outer] (slots per row block) and *max_slots. Every chunk must give each CTA a pair
+ *   (n_outer x narrowest chunk >= g), else EINVAL. */
+int sense_diag_chunk_width(int64_t n_outer, int64_t n_inner, int32_t cp, int32_t g,
+                           int64_t* width);
+int sense_diag_stream_k_layout(int64_t n_outer, int64_t n_inner, int64_t chunk, int32_t g,
+                               int32_t* slot_base, int32_t* nslot, int32_t* max_slots);
+
 const char* sense_strerror(int code);
 const char* sense_last_error(void);
 

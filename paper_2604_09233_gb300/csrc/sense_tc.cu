@@ -742,8 +742,8 @@ static int stream_k_layout(long long n_outer, long long n_inner, long long ch, i
 // of both stages, hi and lo, plus the phase operand; an upper bound) exceed TC_L2_CHUNK_BYTES,
 // then equal chunks below that size, as long as every chunk still gives each of the G CTAs
 // at least one pair.
-static long long chunk_for(const sense_plan_s* P, long long n_outer, long long n_inner, int G) {
-  const long long per_block = 2LL * 2 * 2 * P->Cp * 128 + 16384;
+static long long chunk_for_cp(int Cp, long long n_outer, long long n_inner, int G) {
+  const long long per_block = 2LL * 2 * 2 * Cp * 128 + 16384;
   long long nch = (n_inner * per_block + TC_L2_CHUNK_BYTES - 1) / TC_L2_CHUNK_BYTES;
   if (nch <= 1) return n_inner;
   const long long ch = (n_inner + nch - 1) / nch;
@@ -751,6 +751,10 @@ static long long chunk_for(const sense_plan_s* P, long long n_outer, long long n
   const long long last = n_inner - (nch - 1) * ch;
   if (n_outer * last < G) return n_inner;
   return ch;
+}
+
+static long long chunk_for(const sense_plan_s* P, long long n_outer, long long n_inner, int G) {
+  return chunk_for_cp(P->Cp, n_outer, n_inner, G);
 }
 
 template <int MODE, int CP, int RP, int NPART, bool STORED = false>
@@ -1265,5 +1269,31 @@ extern "C" int sense_plan_store_p(sense_plan P, int32_t enable, void* stream) {
   const int rc = sense::tc_store_p(P, enable != 0, st);
   if (rc != SENSE_OK) return rc;
   SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+  return SENSE_OK;
+}
+
+extern "C" int sense_diag_chunk_width(int64_t n_outer, int64_t n_inner, int32_t cp, int32_t g,
+                                      int64_t* width) {
+  if (!width || n_outer < 1 || n_inner < 1 || cp < 1 || g < 1)
+    return sense::set_error(SENSE_EINVAL, "sizes must be positive and width non-null");
+  *width = sense::chunk_for_cp(cp, n_outer, n_inner, g);
+  return SENSE_OK;
+}
+
+extern "C" int sense_diag_stream_k_layout(int64_t n_outer, int64_t n_inner, int64_t chunk,
+                                          int32_t g, int32_t* slot_base, int32_t* nslot,
+                                          int32_t* max_slots) {
+  if (!slot_base || !nslot || !max_slots || n_outer < 1 || n_inner < 1 || chunk < 1 || g < 1)
+    return sense::set_error(SENSE_EINVAL, "sizes must be positive and outputs non-null");
+  const long long nch = (n_inner + chunk - 1) / chunk;
+  const long long narrowest = std::min<long long>(chunk, n_inner - (nch - 1) * chunk);
+  if (n_outer * narrowest < g)
+    return sense::set_error(SENSE_EINVAL, "a chunk gives some CTA no pair");
+  std::vector<int> base, ns;
+  int mx = 0;
+  sense::stream_k_layout(n_outer, n_inner, chunk, g, base, ns, &mx);
+  std::copy(base.begin(), base.end(), slot_base);
+  std::copy(ns.begin(), ns.end(), nslot);
+  *max_slots = mx;
   return SENSE_OK;
 }

@@ -34,7 +34,8 @@ EXPORTED = ["sense_plan_create", "sense_plan_destroy", "sense_plan_set_b0", "sen
             "sense_batch_normal_op", "sense_batch_cg_solve", "sense_batch_set_tuning",
             "sense_batch_autotune", "sense_cg_solve_iterates", "sense_kspace_filter_mask",
             "sense_kspace_filter", "sense_plan_store_p", "sense_smooth_map",
-            "sense_kspace_filter_mask3d", "sense_smooth_sensitivities"]
+            "sense_kspace_filter_mask3d", "sense_smooth_sensitivities", "sense_diag_chunk_width",
+            "sense_diag_stream_k_layout"]
 
 
 class SenseError(RuntimeError):
@@ -136,6 +137,9 @@ def _load():
         "sense_plan_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "sense_plan_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
         "sense_diag_sincos_rate": ([dbl, ctypes.POINTER(dbl)], ctypes.c_int),
+        "sense_diag_chunk_width": ([i64, i64, i32, i32, ctypes.POINTER(i64)], ctypes.c_int),
+        "sense_diag_stream_k_layout": ([i64, i64, i64, i32, vp, vp, ctypes.POINTER(i32)],
+                                       ctypes.c_int),
         "sense_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sense_last_error": ([], ctypes.c_char_p),
     }
@@ -592,6 +596,27 @@ def sense_diag_sincos_rate(ms_budget=200.0):
     _check(_lib.sense_diag_sincos_rate(float(ms_budget), ctypes.byref(v)),
            "sense_diag_sincos_rate")
     return v.value
+
+
+def sense_diag_chunk_width(n_outer, n_inner, cp, g):
+    """Streamed blocks per stream-K chunk of a tensor-core pass (host only)."""
+    w = ctypes.c_int64()
+    _check(_lib.sense_diag_chunk_width(int(n_outer), int(n_inner), int(cp), int(g),
+                                       ctypes.byref(w)), "sense_diag_chunk_width")
+    return w.value
+
+
+def sense_diag_stream_k_layout(n_outer, n_inner, chunk, g):
+    """Slot bases [chunks][n_outer], slots per row block and the largest slot count of the
+    chunked stream-K schedule (host only)."""
+    nch = (int(n_inner) + int(chunk) - 1) // int(chunk)
+    base = np.zeros((nch, int(n_outer)), np.int32)
+    nslot = np.zeros(int(n_outer), np.int32)
+    mx = ctypes.c_int32()
+    _check(_lib.sense_diag_stream_k_layout(int(n_outer), int(n_inner), int(chunk), int(g),
+                                           base.ctypes.data, nslot.ctypes.data,
+                                           ctypes.byref(mx)), "sense_diag_stream_k_layout")
+    return base, nslot, mx.value
 
 
 def sense_strerror(code):
