@@ -37,12 +37,62 @@ struct sense_batch_s {
   cudaGraphExec_t gexec = nullptr;
   int graph_prec = -1;
   std::vector<int64_t> geom_versions;  // of each plan when the descriptors were built
+  // side streams for the instances' small kernels, and the events that fork them from and
+  // join them back into the caller's stream (a set per fork site of one CG iteration)
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> events;   // [FORK_SITES][1 + side.size()]
 };
 
 namespace sense {
 namespace {
 
 constexpr int CHUNK_CANDIDATES[] = {8, 16, 32, 64};
+constexpr int MAX_SIDE_STREAMS = 16;
+constexpr int FORK_SITES = 3;  // per CG iteration: B images of p; Y and its image; reduction + CG
+
+// Run fn(b, stream) for every instance b, spread round-robin over the batch's side streams,
+// which wait for everything issued on st so far; st then waits for all of them. The instances'
+// small kernels (a few blocks each) so run concurrently instead of one after another, and in a
+// captured CUDA graph they form parallel branches. `site` selects the events of this fork.
+template <class F>
+int for_instances(sense_batch_s* B, int site, cudaStream_t st, F&& fn) {
+  const int n = (int)B->plans.size();
+  const int S = (int)B->side.size();
+  if (S == 0) {
+    for (int b = 0; b < n; ++b) {
+      const int rc = fn(b, st);
+      if (rc != SENSE_OK) return rc;
+    }
+    return SENSE_OK;
+  }
+  cudaEvent_t* ev = &B->events[(size_t)site * (1 + S)];
+  SENSE_CUDA_TRY(cudaEventRecord(ev[0], st));
+  for (int k = 0; k < S; ++k) SENSE_CUDA_TRY(cudaStreamWaitEvent(B->side[k], ev[0], 0));
+  int rc = SENSE_OK;
+  for (int b = 0; b < n && rc == SENSE_OK; ++b) rc = fn(b, B->side[b % S]);
+  // join even after a failure, so that no side stream is left outside a capture
+  for (int k = 0; k < S; ++k) {
+    SENSE_CUDA_TRY(cudaEventRecord(ev[1 + k], B->side[k]));
+    SENSE_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + k], 0));
+  }
+  return rc;
+}
+
+int create_side_streams(sense_batch_s* B) {
+  const int S = std::min<int>((int)B->plans.size(), MAX_SIDE_STREAMS);
+  if (S < 2) return SENSE_OK;
+  for (int k = 0; k < S; ++k) {
+    cudaStream_t s;
+    SENSE_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    B->side.push_back(s);
+  }
+  for (int e = 0; e < FORK_SITES * (1 + S); ++e) {
+    cudaEvent_t ev;
+    SENSE_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    B->events.push_back(ev);
+  }
+  return SENSE_OK;
+}
 constexpr int SEG_CANDIDATES[] = {2, 4};
 
 int dmalloc(void** p, size_t bytes, const char* what) {
@@ -174,34 +224,35 @@ int batch_pass(sense_batch_s* B, int mode, int npart, bool with_stop, cudaStream
 // q_b = E_b^H E_b p_b for every instance b (plan-order vectors of each plan); with_stop:
 // instances whose CG has stopped are skipped.
 int batch_normal(sense_batch_s* B, int prec, const std::vector<const float2*>& p,
-                 const std::vector<float2*>& q, bool with_stop, cudaStream_t st) {
+                 const std::vector<float2*>& q, bool with_stop, cudaStream_t st,
+                 bool reduce_x = true) {
   const int np = prec == SENSE_PREC_TC_SPLIT ? 2 : 1;
-  const int n = (int)B->plans.size();
   int rc;
-  for (int b = 0; b < n; ++b) {
-    sense_plan_s* P = B->plans[b];
-    if ((rc = tc_make_image(P, np, nullptr, p[b], P->Lp, P->colmax, P->qscale, P->Qimg, false,
-                            st)))
-      return rc;
-  }
+  if ((rc = for_instances(B, 0, st, [&](int b, cudaStream_t s) {
+         sense_plan_s* P = B->plans[b];
+         return tc_make_image(P, np, nullptr, p[b], P->Lp, P->colmax, P->qscale, P->Qimg, false,
+                              s);
+       })))
+    return rc;
   if ((rc = batch_pass(B, tc::ENC, np, with_stop, st))) return rc;
-  for (int b = 0; b < n; ++b) {
-    sense_plan_s* P = B->plans[b];
-    const double* stop = with_stop ? P->scal + SC_STOP : nullptr;
-    if ((rc = tc_reduce_y(P, B->ypart[b], B->nslot_e[b], P->Y, nullptr, P->colmax + P->Cp, stop,
-                          st)))
-      return rc;
-    if ((rc = tc_make_image(P, np, P->Y, nullptr, P->Kp, P->colmax + P->Cp, P->yscale, P->Yimg,
-                            true, st)))
-      return rc;
-  }
+  if ((rc = for_instances(B, 1, st, [&](int b, cudaStream_t s) {
+         sense_plan_s* P = B->plans[b];
+         const double* stop = with_stop ? P->scal + SC_STOP : nullptr;
+         int r = tc_reduce_y(P, B->ypart[b], B->nslot_e[b], P->Y, nullptr, P->colmax + P->Cp,
+                             stop, s);
+         if (r == SENSE_OK)
+           r = tc_make_image(P, np, P->Y, nullptr, P->Kp, P->colmax + P->Cp, P->yscale, P->Yimg,
+                             true, s);
+         return r;
+       })))
+    return rc;
   if ((rc = batch_pass(B, tc::ADJ, np, with_stop, st))) return rc;
-  for (int b = 0; b < n; ++b) {
+  if (!reduce_x) return SENSE_OK;
+  return for_instances(B, 2, st, [&](int b, cudaStream_t s) {
     sense_plan_s* P = B->plans[b];
     const double* stop = with_stop ? P->scal + SC_STOP : nullptr;
-    if ((rc = tc_reduce_x(P, B->xpart[b], B->nslot_a[b], q[b], stop, st))) return rc;
-  }
-  return SENSE_OK;
+    return tc_reduce_x(P, B->xpart[b], B->nslot_a[b], q[b], stop, s);
+  });
 }
 
 // one CG iteration (E^H E p, step length, updates, direction) of every instance
@@ -213,13 +264,16 @@ int batch_cg_iteration(sense_batch_s* B, int prec, cudaStream_t st) {
     q.push_back(P->vq);
   }
   int rc;
-  if ((rc = batch_normal(B, prec, p, q, true, st))) return rc;
-  for (auto* P : B->plans) {
-    if ((rc = cg_step_alpha(P, st)) || (rc = cg_step_update(P, nullptr, st)) ||
-        (rc = cg_step_p(P, st)))
-      return rc;
-  }
-  return SENSE_OK;
+  if ((rc = batch_normal(B, prec, p, q, true, st, false))) return rc;
+  // per instance: the E^H reduction into q, then the CG step length, updates and direction
+  return for_instances(B, 2, st, [&](int b, cudaStream_t s) {
+    sense_plan_s* P = B->plans[b];
+    int r = tc_reduce_x(P, B->xpart[b], B->nslot_a[b], q[b], P->scal + SC_STOP, s);
+    if (r == SENSE_OK) r = cg_step_alpha(P, s);
+    if (r == SENSE_OK) r = cg_step_update(P, nullptr, s);
+    if (r == SENSE_OK) r = cg_step_p(P, s);
+    return r;
+  });
 }
 
 int check_err(sense_batch_s* B) {
@@ -251,6 +305,8 @@ int check_batch(sense_batch_s* B) {
 void batch_free(sense_batch_s* B) {
   if (!B) return;
   free_layout(B);
+  for (auto s : B->side) cudaStreamDestroy(s);
+  for (auto e : B->events) cudaEventDestroy(e);
   cudaFree(B->qnext);
   cudaFree(B->err);
   for (auto* P : B->plans) sense_plan_destroy(P);
@@ -305,6 +361,7 @@ extern "C" int sense_batch_create(const sense_problem* probs, int32_t n, sense_b
   if (rc == SENSE_OK && cudaMemset(B->err, 0, 4) != cudaSuccess)
     rc = cuda_error(cudaGetLastError(), "cudaMemset");
   if (rc == SENSE_OK) rc = build_layout(B);
+  if (rc == SENSE_OK) rc = create_side_streams(B);
   if (rc != SENSE_OK) {
     batch_free(B);
     return rc;
