@@ -263,18 +263,18 @@ def run_reference(args):
 # by the SHA-256 of the pass-kernel source they were taken on (pass_kernel_source_hash); any other
 # source reports null.
 KERNEL_TRAFFIC = {
-    "e076f38bb4391122a9cdb4d1d291b66f5b0b90e219d3fb6b0e1a3f12d9714084": {
+    "6f4586b88a18f9ea82086326cf942c8d5ea6f378e416f2b19f8c856d6f945ea7": {
         "2d_256x256_32coil_35750samp_sh3": {
             "precision": "tc_split",
-            "tc_encode_pass": 174706432 + 8401152,
-            "tc_adjoint_pass": 169117184 + 9986560,
-            "inst_tc_encode_pass": 1420550033,
-            "inst_tc_adjoint_pass": 1420752711,
+            "tc_encode_pass": 175048960 + 8707072,
+            "tc_adjoint_pass": 169221376 + 10060288,
+            "inst_tc_encode_pass": 1413535812,
+            "inst_tc_adjoint_pass": 1413884787,
             # stored-P passes (the NKP = 0 instantiation of the same source): one capture of
             # `python bench.py --op-only --stored --steps 1 --warmup 1`
             # (profiles/tcp_pass_stored_2d256_32coil.md)
-            "stored_tc_encode_pass": 19920000000 + 13000000,
-            "stored_tc_adjoint_pass": 19570000000 + 18030000,
+            "stored_tc_encode_pass": 19943396352 + 13079808,
+            "stored_tc_adjoint_pass": 19573116928 + 17617920,
         },
     },
 }

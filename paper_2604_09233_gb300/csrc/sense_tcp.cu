@@ -16,10 +16,11 @@
 // with the B operand as before. The E^H pass writes the tile of e^{+i phi} and takes the
 // conjugate in the accumulator read-out.
 // Per CTA (one per SM, persistent, 20 warps):
-//   16 generator warps  : phases out of TMEM -> anchors -> sin/cos -> FP16 tile into TMEM; at
-//                         segment ends they drain the accumulators into running sums, and at
-//                         run ends write the run's rows per coil (both passes; the E^H pass's
-//                         coil combine with S is done by the slot reduction);
+//   16 generator warps  : phases out of TMEM -> anchors -> sin/cos -> FP16 tile into TMEM (for
+//                         single tiles in two groups of 8 on alternating stages); at segment
+//                         ends they drain the accumulators into running sums, and at run ends
+//                         write the run's rows per coil (both passes; the E^H pass's coil
+//                         combine with S is done by the slot reduction);
 //   1 phase warp        : the phase MMAs of the stages ahead (A and B in shared memory), each
 //                         into the TMEM slot of its stage once that slot's contraction is done;
 //   2 contraction warps : the contraction MMAs of each stage (A in TMEM, B in shared memory),
@@ -88,6 +89,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   // NKP = 0: stored-P variant: the tiles are read from HBM (written by a generating pass with
   // Params::emit), no phase operands or anchors are loaded and no phase MMAs run
   constexpr bool STORED = NKP == 0;
+  // generator groups on alternating stages: two for single tiles, one for split tiles
+  constexpr int GROUPS = NPART == 1 ? 2 : 1;
+  constexpr int GEN_PER_STAGE = NGEN_WARPS / GROUPS;  // generator warps that write a stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sB = base;                                     // [NBUF][B_BYTES]
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
   uint8_t* sPr = sPc + NBUF * LY::PC_BYTES;               // [2][PR_BYTES]
   float* sAnc = (float*)(sPr + 2 * LY::PR_BYTES);         // [NBUF][128] streamed anchors
   float* sRowAnc = sAnc + NBUF * 128;                     // [NBUF][128] row anchors
-  float2* sRacc = (float2*)(sRowAnc + NBUF * 128);        // [CP/4][512]
+  float2* sRacc = (float2*)(sRowAnc + NBUF * 128);        // [CP/4][512] running sums
   Meta* sMeta = (Meta*)(sRacc + CW * NGEN_WARPS * 32);    // [NBUF]
   uint64_t* bars = (uint64_t*)(sMeta + NBUF);
   uint64_t* full = bars;                 // [NBUF] streamed block landed
@@ -131,11 +135,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     }
     for (int s = 0; s < NSLOT; ++s) {
       mbar_init(smem_u32(&pfull[s]), 1);
-      mbar_init(smem_u32(&tfull[s]), NGEN_WARPS);
+      mbar_init(smem_u32(&tfull[s]), GEN_PER_STAGE);
       mbar_init(smem_u32(&tempty[s]), 2);
     }
     mbar_init(smem_u32(afull), 2);
-    mbar_init(smem_u32(aempty), NGEN_WARPS);
+    mbar_init(smem_u32(aempty), GEN_PER_STAGE);  // the drainers (group 0)
     for (int r = 0; r < 3; ++r) mbar_init(smem_u32(drain + r), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -424,13 +428,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
     }
   } else {
     // ------------------------------------------------------------------ generators
-    const int g = warp >> 2;  // warpgroup: K-step of every 64-wide stage
+    // Split tiles: all 16 warps generate every stage; warp w covers the 32 rows of its TMEM
+    // lane quarter (w & 3) and K-step w >> 2 (16 elements) of the stage's 64. Single tiles:
+    // two groups of 8 warps on alternating stages (group grp generates stage grp of every
+    // block, warp w K-steps 2h, 2h + 1 with h = (w >> 2) & 1), so that one group's barrier
+    // waits overlap the other group's arithmetic; group 0 drains. (With the three times
+    // longer split contraction the groups gain nothing: the slots, not the generators, set the
+    // pace there.)
+    constexpr int NST = GROUPS == 2 ? 1 : 2;  // stages of a block that a warp generates
+    constexpr int NKS = GROUPS == 2 ? 2 : 1;  // K-steps of a stage that a warp generates
+    constexpr int NDT = GEN_PER_STAGE * 32;   // threads that drain
+    const int grp = GROUPS == 2 ? warp >> 3 : 0;
+    const int g0 = GROUPS == 2 ? ((warp >> 2) & 1) * 2 : warp >> 2;  // first K-step
+    const bool drainer = grp == 0;
     const int row = ((warp & 3) << 5) + lane;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const int cbase = g * CW;
+    const int cbase = g0 * CW;  // a drainer's coils: [cbase, cbase + NKS CW)
     const uint16_t M1 = 0xBC00u;  // -1 in FP16
     float2* racc = sRacc + threadIdx.x;
-    constexpr int NGT = NGEN_WARPS * 32;
     int pending = -1;
     auto flush_pending = [&]() {
       if (pending >= 0) {
@@ -442,14 +457,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       }
     };
     Ring<NBUF> rb;
-    Ring<NSLOT> rs;
+    Ring<NSLOT> rs;  // the slot of this warp's next stage
+    if (grp == 1) rs.next();
     int seg = 0, seg_pos = 0;  // segments drained; position of the block in its segment
     bool ok = true;
     // the next block's data / the next stage's phases, found ready by a test made during the
-    // previous stage's arithmetic (so that the test's latency is hidden behind it)
+    // current stage's arithmetic (so that the test's latency is hidden behind it)
     bool next_full = false, next_pfull = false;
+    if (drainer) {
 #pragma unroll
-    for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
+      for (int c = 0; c < NKS * CW; ++c) racc[c * NDT] = make_float2(0.f, 0.f);
+    }
     bool drain_due = false, d_out = false;
     int d_b = 0, d_slot = 0;
     long long d_row = 0;
@@ -460,26 +478,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       drain_due = false;
       if (!warp_wait(smem_u32(afull), (uint32_t)seg & 1u, abort_flag, p.err, 7, LIM)) return false;
       tc_fence_after();
-      float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
       const uint32_t lb = tmem + lane_base;
-      tmem_ld<CW>(lb + cbase, d1r);               // D1[:, c]      = A_re B_re
-      tmem_ld<CW>(lb + CP + cbase, d1i);          // D1[:, C+c]    = A_re B_im
-      tmem_ld<CW>(lb + NM + cbase, d2r);          // D2[:, c]      = A_im B_re
-      tmem_ld<CW>(lb + NM + CP + cbase, d2i);     // D2[:, C+c]    = A_im B_im
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(aempty));
 #pragma unroll
-      for (int c = 0; c < CW; ++c) {
-        float2 a = racc[c * NGT];
-        if (MODE == ENC) {
-          a.x += d1r[c] - d2i[c];
-          a.y += d1i[c] + d2r[c];
-        } else {
-          a.x += d1r[c] + d2i[c];
-          a.y += d1i[c] - d2r[c];
+      for (int gi = 0; gi < NKS; ++gi) {
+        const int cb = cbase + gi * CW;
+        float d1r[CW], d1i[CW], d2r[CW], d2i[CW];
+        tmem_ld<CW>(lb + cb, d1r);               // D1[:, c]      = A_re B_re
+        tmem_ld<CW>(lb + CP + cb, d1i);          // D1[:, C+c]    = A_re B_im
+        tmem_ld<CW>(lb + NM + cb, d2r);          // D2[:, c]      = A_im B_re
+        tmem_ld<CW>(lb + NM + CP + cb, d2i);     // D2[:, C+c]    = A_im B_im
+        if (gi == NKS - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(aempty));
         }
-        racc[c * NGT] = a;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          float2 a = racc[(gi * CW + c) * NDT];
+          if (MODE == ENC) {
+            a.x += d1r[c] - d2i[c];
+            a.y += d1i[c] + d2r[c];
+          } else {
+            a.x += d1r[c] + d2i[c];
+            a.y += d1i[c] - d2r[c];
+          }
+          racc[(gi * CW + c) * NDT] = a;
+        }
       }
       ++seg;
       if (!d_out) return true;
@@ -489,13 +513,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       const InstDesc& d = desc(d_b);
       float2* dst = d.out + ((long long)d_slot * d.rows_total + d_row) * CP + cbase;
 #pragma unroll
-      for (int c = 0; c < CW; ++c) {
+      for (int c = 0; c < NKS * CW; ++c) {
         const float sc = d.bscale[cbase + c];
-        const float2 a = racc[c * NGT];
+        const float2 a = racc[c * NDT];
         dst[c] = make_float2(a.x * sc, a.y * sc);
       }
 #pragma unroll
-      for (int c = 0; c < CW; ++c) racc[c * NGT] = make_float2(0.f, 0.f);
+      for (int c = 0; c < NKS * CW; ++c) racc[c * NDT] = make_float2(0.f, 0.f);
       return true;
     };
     for (;; rb.next()) {
@@ -517,11 +541,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
       const float2 rb2 = make_float2(ranc, ranc);
       uint4* emit = EMIT ? p.emit + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
                          : nullptr;
-      // stored tiles of this pair: 16 chunks (stage, warpgroup, half) of [4][128] uint4
+      // stored tiles of this pair: 16 chunks (stage, K-step, half) of [4][128] uint4
       const uint4* ptile =
           STORED ? dm.stored + ((long long)m.o * dm.n_inner + m.in) * (16 * 4 * 128) + row
                  : nullptr;
-      for (int st = 0; st < 2; ++st, rs.next()) {
+      for (int sti = 0; sti < NST; ++sti, rs.next()) {
+        const int st = GROUPS == 2 ? grp : sti;
         const int slot = rs.idx;
         if (!next_pfull && !warp_wait(smem_u32(&pfull[slot]), rs.phase, abort_flag, p.err, 6, LIM)) {
           ok = false;
@@ -529,118 +554,121 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_pass_kernel(Params p) {
         }
         next_pfull = false;
         tc_fence_after();
-        const uint32_t acol = tmem + lane_base + LY::ACOL0 + slot * LY::SLOT_COLS + g * 8;
-        if (STORED) {
-          // both halves' tiles, loaded before any of them is stored
-          uint4 v[2][4];
 #pragma unroll
-          for (int jh = 0; jh < 2; ++jh) {
-            const uint4* c = ptile + (((st * 4 + g) * 2 + jh) * 4) * 128;
-            v[jh][0] = __ldg(c);
-            v[jh][2] = __ldg(c + 2 * 128);
-            if (NPART == 2) {
-              v[jh][1] = __ldg(c + 128);
-              v[jh][3] = __ldg(c + 3 * 128);
+        for (int gi = 0; gi < NKS; ++gi) {
+          const int g = g0 + gi;
+          const uint32_t acol = tmem + lane_base + LY::ACOL0 + slot * LY::SLOT_COLS + g * 8;
+          if (STORED) {
+            // both halves' tiles, loaded before any of them is stored
+            uint4 v[2][4];
+#pragma unroll
+            for (int jh = 0; jh < 2; ++jh) {
+              const uint4* c = ptile + (((st * 4 + g) * 2 + jh) * 4) * 128;
+              v[jh][0] = __ldg(c);
+              v[jh][2] = __ldg(c + 2 * 128);
+              if (NPART == 2) {
+                v[jh][1] = __ldg(c + 128);
+                v[jh][3] = __ldg(c + 3 * 128);
+              }
             }
+#pragma unroll
+            for (int jh = 0; jh < 2; ++jh) {
+              const uint32_t re_hi[4] = {v[jh][0].x, v[jh][0].y, v[jh][0].z, v[jh][0].w};
+              const uint32_t im_hi[4] = {v[jh][2].x, v[jh][2].y, v[jh][2].z, v[jh][2].w};
+              const uint32_t hcol = acol + 4 * jh;
+              if (NPART == 2) {
+                const uint32_t re_lo[4] = {v[jh][1].x, v[jh][1].y, v[jh][1].z, v[jh][1].w};
+                const uint32_t im_lo[4] = {v[jh][3].x, v[jh][3].y, v[jh][3].z, v[jh][3].w};
+                tmem_st4(hcol + 0, re_hi);
+                tmem_st4(hcol + 32, re_lo);
+                tmem_st4(hcol + 64, im_hi);
+                tmem_st4(hcol + 96, im_lo);
+              } else {
+                tmem_st4(hcol + 0, re_hi);
+                tmem_st4(hcol + 32, im_hi);
+              }
+            }
+            continue;
           }
+          // this thread's 16 phases of K-step g: elements 0..7 in columns [8g, 8g+8), 8..15
+          // in [32+8g, ..)
+          float dv[16];
+          tmem_ld8x2(acol, acol + 32, dv);
 #pragma unroll
           for (int jh = 0; jh < 2; ++jh) {
-            const uint32_t re_hi[4] = {v[jh][0].x, v[jh][0].y, v[jh][0].z, v[jh][0].w};
-            const uint32_t im_hi[4] = {v[jh][2].x, v[jh][2].y, v[jh][2].z, v[jh][2].w};
+            if (gi == NKS - 1 && jh == 1) {
+              // what this warp's next stage waits for: at a block's end the next block's
+              // data, and its phases (each barrier observed directly, for the ordering of
+              // what it guards)
+              const bool block_end = sti == NST - 1;
+              if (block_end) {
+                const Ring<NBUF> nb = rb.peek();
+                next_full = warp_test(smem_u32(&full[nb.idx]), nb.phase);
+              }
+              const Ring<NSLOT> nr = GROUPS == 2 ? rs.peek().peek() : rs.peek();
+              next_pfull =
+                  (!block_end || next_full) && warp_test(smem_u32(&pfull[nr.idx]), nr.phase);
+            }
+            uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+            const int v0 = st * 64 + g * 16 + 8 * jh;
+            const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
+            const float4 a8 = *reinterpret_cast<const float4*>(anc + v0 + 4);
+            const float2 an[4] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w),
+                                  make_float2(a8.x, a8.y), make_float2(a8.z, a8.w)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              // phase (radians) = D + A + B; not range-reduced: |A|, |B| <= pi and |D| is a
+              // few turns, within the argument range the sine unit handles at this accuracy
+              float2 t = __ffma2_rn(make_float2(dv[8 * jh + 2 * k], dv[8 * jh + 2 * k + 1]),
+                                    us2, an[k]);
+              t = __fadd2_rn(t, rb2);
+              float2 cs, sn;
+              __sincosf(t.x, &sn.x, &cs.x);
+              __sincosf(t.y, &sn.y, &cs.y);
+              re_hi[k] = pack_h2(cs.x, cs.y);
+              im_hi[k] = pack_h2(sn.x, sn.y);
+              if (NPART == 2) {
+                // lo = v - hi exactly in FP32 (hi holds 11 significant bits of v), then FP16
+                const uint32_t hc = re_hi[k], hs = im_hi[k];
+                re_lo[k] = pack_h2(fma_f16_f32((uint16_t)(hc & 0xFFFFu), M1, cs.x),
+                                   fma_f16_f32((uint16_t)(hc >> 16), M1, cs.y));
+                im_lo[k] = pack_h2(fma_f16_f32((uint16_t)(hs & 0xFFFFu), M1, sn.x),
+                                   fma_f16_f32((uint16_t)(hs >> 16), M1, sn.y));
+              }
+            }
+            __syncwarp();
             const uint32_t hcol = acol + 4 * jh;
             if (NPART == 2) {
-              const uint32_t re_lo[4] = {v[jh][1].x, v[jh][1].y, v[jh][1].z, v[jh][1].w};
-              const uint32_t im_lo[4] = {v[jh][3].x, v[jh][3].y, v[jh][3].z, v[jh][3].w};
               tmem_st4(hcol + 0, re_hi);
               tmem_st4(hcol + 32, re_lo);
               tmem_st4(hcol + 64, im_hi);
               tmem_st4(hcol + 96, im_lo);
+              if (EMIT) {
+                uint4* dst = emit + (((st * 4 + g) * 2 + jh) * 4) * 128;
+                dst[0] = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+                dst[128] = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+                dst[256] = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+                dst[384] = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+              }
             } else {
               tmem_st4(hcol + 0, re_hi);
               tmem_st4(hcol + 32, im_hi);
             }
           }
-          pending = slot;
-          flush_pending();
-          if (st == 0 && drain_due && !drain()) {
-            ok = false;
-            break;
-          }
-          continue;
-        }
-        // this thread's 16 phases: elements 0..7 in columns [8g, 8g+8), 8..15 in [32+8g, ..)
-        float dv[16];
-        tmem_ld8x2(acol, acol + 32, dv);
-#pragma unroll
-        for (int jh = 0; jh < 2; ++jh) {
-          if (jh == 1) {
-            // what the next stage waits for: at a block's end the next block's data, and its
-            // phases (each barrier observed directly, for the ordering of what it guards)
-            const Ring<NSLOT> nr = rs.peek();
-            if (st == 1) {
-              const Ring<NBUF> nb = rb.peek();
-              next_full = warp_test(smem_u32(&full[nb.idx]), nb.phase);
-            }
-            next_pfull = (st == 0 || next_full) && warp_test(smem_u32(&pfull[nr.idx]), nr.phase);
-          }
-          uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
-          const int v0 = st * 64 + g * 16 + 8 * jh;
-          const float4 a4 = *reinterpret_cast<const float4*>(anc + v0);
-          const float4 a8 = *reinterpret_cast<const float4*>(anc + v0 + 4);
-          const float2 an[4] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w),
-                                make_float2(a8.x, a8.y), make_float2(a8.z, a8.w)};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            // phase (radians) = D + A + B; not range-reduced: |A|, |B| <= pi and |D| is a
-            // few turns, within the argument range the sine unit handles at this accuracy
-            float2 t = __ffma2_rn(make_float2(dv[8 * jh + 2 * k], dv[8 * jh + 2 * k + 1]), us2,
-                                  an[k]);
-            t = __fadd2_rn(t, rb2);
-            float2 cs, sn;
-            __sincosf(t.x, &sn.x, &cs.x);
-            __sincosf(t.y, &sn.y, &cs.y);
-            re_hi[k] = pack_h2(cs.x, cs.y);
-            im_hi[k] = pack_h2(sn.x, sn.y);
-            if (NPART == 2) {
-              // lo = v - hi exactly in FP32 (hi holds 11 significant bits of v), then FP16
-              const uint32_t hc = re_hi[k], hs = im_hi[k];
-              re_lo[k] = pack_h2(fma_f16_f32((uint16_t)(hc & 0xFFFFu), M1, cs.x),
-                                 fma_f16_f32((uint16_t)(hc >> 16), M1, cs.y));
-              im_lo[k] = pack_h2(fma_f16_f32((uint16_t)(hs & 0xFFFFu), M1, sn.x),
-                                 fma_f16_f32((uint16_t)(hs >> 16), M1, sn.y));
-            }
-          }
-          __syncwarp();
-          const uint32_t hcol = acol + 4 * jh;
-          if (NPART == 2) {
-            tmem_st4(hcol + 0, re_hi);
-            tmem_st4(hcol + 32, re_lo);
-            tmem_st4(hcol + 64, im_hi);
-            tmem_st4(hcol + 96, im_lo);
-            if (EMIT) {
-              uint4* dst = emit + (((st * 4 + g) * 2 + jh) * 4) * 128;
-              dst[0] = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
-              dst[128] = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
-              dst[256] = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
-              dst[384] = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
-            }
-          } else {
-            tmem_st4(hcol + 0, re_hi);
-            tmem_st4(hcol + 32, im_hi);
-          }
         }
         pending = slot;
         flush_pending();
-        if (st == 0 && drain_due && !drain()) {
+        if (sti == 0 && drain_due && !drain()) {
           ok = false;
           break;
         }
       }
       if (!ok) break;
+      if (GROUPS == 2) rs.next();  // past the other group's stage of the block
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[buf]));
-      if (seg_last) {
-        // drain after the next stage has been generated (or at the end)
+      if (seg_last && drainer) {
+        // drain after this warp's next stage has been generated (or at the end)
         drain_due = true;
         d_out = (m.flags & META_LAST) != 0;
         d_b = m.inst;
