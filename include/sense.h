@@ -358,7 +358,8 @@ int sense_plan_store_p(sense_plan plan, int32_t enable, void* stream);
  * (no counterpart in the paper: execution parameters of the tensor-core kernels)
  *   seg_len  the tensor-core passes accumulate at most this many 128 x 128 (sample, voxel)
  *            blocks in one FP32 tensor-memory accumulator before adding it to a running
- *            sum; shorter = more accurate, longer = fewer drains. 1..64, default 4.
+ *            sum; shorter = more accurate, longer = fewer drains. 1..64, or 0 = by precision
+ *            (default): 4 for TC_SPLIT, 16 for TC_FP16 (whose FP16 rounding dominates).
  *   grid     persistent CTAs of a tensor-core pass; 0 = one per SM (default).
  *   wait_limit_us  every wait inside a tensor-core pass gives up after this long (measured
  *            in SM clock cycles at the maximum clock); the CTA then records the failure,

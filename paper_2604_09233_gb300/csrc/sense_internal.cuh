@@ -130,7 +130,8 @@ struct sense_plan_s {
   // tensor-core path (sense_tc.cu)
   int tc_grid = 0;                 // persistent CTAs launched (<= pairs of blocks)
   int tc_grid_req = 0;             // requested CTAs (one per SM by default)
-  int tc_seg_len = 4;              // drain the TMEM accumulators every this many pairs
+  int tc_seg_len = 0;              // drain the TMEM accumulators every this many pairs (0: by
+                                   // precision, tc_seg_for)
   int tc_wait_us = 0;              // bounded-wait limit of the tensor-core kernels (0: ~2 s)
   long long tc_wait_cycles = 0;    // the same in SM clock cycles (0: the kernel's default)
   int tc_test_hold = 0;            // time-out tests: stage CTA 0's loader withholds (+1)

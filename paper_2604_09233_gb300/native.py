@@ -570,7 +570,7 @@ def sense_plan_get_tuning(plan):
             "test_hold_stage": t.test_hold_stage, "inner_chunk": t.inner_chunk}
 
 
-def sense_plan_set_tuning(plan, seg_len=4, grid=0, wait_limit_us=0, test_hold_stage=0,
+def sense_plan_set_tuning(plan, seg_len=0, grid=0, wait_limit_us=0, test_hold_stage=0,
                           inner_chunk=0):
     t = Tuning(int(seg_len), int(grid), int(wait_limit_us), int(test_hold_stage),
                int(inner_chunk))
